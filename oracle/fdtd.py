@@ -1,0 +1,103 @@
+"""ctypes front end of the FP64 C oracle for K and K* (test infrastructure only).
+
+Paper Sec. 2.2: K maps the initial pressure p0 (N cells) to the sensor traces
+y in R^{Ns x Nt}; here the wave IVP of Eq. (wave_equation) is discretised as
+the literal staggered pressure/velocity leapfrog described in fdtd.c, and K*
+is the reverse sweep of that program (its exact transpose).
+"""
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        sig = [ctypes.c_int, ip, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+               dp, dp, dp]
+        for name in ("oracle_forward", "oracle_adjoint"):
+            f = getattr(_lib, name)
+            f.argtypes = sig
+            f.restype = ctypes.c_int
+        _lib.oracle_forward_history.argtypes = [ctypes.c_int, ip, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_int, dp, dp, dp]
+        _lib.oracle_forward_history.restype = ctypes.c_int
+        _lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib.oracle_max_threads.restype = ctypes.c_int
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Wave:
+    """Geometry + medium of one problem.
+
+    shape: grid shape in array order, (ny, nx) or (nz, ny, nx), x fastest.
+    h: spacing [m]; dt: time step [s]; nt: number of samples (P^0 .. P^{nt-1});
+    order: 2, 4, 6 or 8; c: scalar or array of shape `shape` [m/s];
+    sensors: (Ns, dim) coordinates (x, y[, z]) in metres, cell i at i*h.
+    """
+
+    def __init__(self, shape, h, dt, nt, order, c, sensors):
+        self.shape = tuple(int(s) for s in shape)
+        self.dim = len(self.shape)
+        self.h, self.dt, self.nt, self.order = float(h), float(dt), int(nt), int(order)
+        c = np.asarray(c, dtype=np.float64)
+        self.c = np.ascontiguousarray(np.broadcast_to(c, self.shape), dtype=np.float64)
+        self.sensors = np.ascontiguousarray(np.asarray(sensors, dtype=np.float64).reshape(-1, self.dim))
+        self.ns = self.sensors.shape[0]
+        self.n3 = np.array(list(self.shape[::-1]) + [1] * (3 - self.dim), dtype=np.int32)
+        self.N = int(np.prod(self.shape))
+        self.evaluations = 0  # wave-equation solves performed (forward or adjoint)
+
+    def _args(self):
+        return (self.dim, self.n3.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.h, self.dt, self.nt,
+                self.order, _dp(self.c), self.ns, _dp(self.sensors))
+
+    def forward(self, x):
+        """y = K x, shape (Ns, nt)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(self.shape))
+        y = np.zeros((self.ns, self.nt), dtype=np.float64)
+        rc = _load().oracle_forward(*self._args(), _dp(x), _dp(y))
+        if rc != 0:
+            raise ValueError(f"oracle_forward failed ({rc})")
+        self.evaluations += 1
+        return y
+
+    def adjoint(self, y):
+        """x = K* y, shape `shape`."""
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(self.ns, self.nt))
+        x = np.zeros(self.shape, dtype=np.float64)
+        rc = _load().oracle_adjoint(*self._args(), _dp(y), _dp(x))
+        if rc != 0:
+            raise ValueError(f"oracle_adjoint failed ({rc})")
+        self.evaluations += 1
+        return x
+
+    def history(self, x):
+        """All pressure fields P^0..P^{nt-1}, shape (nt,) + shape."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(self.shape))
+        hist = np.zeros((self.nt,) + self.shape, dtype=np.float64)
+        lib = _load()
+        rc = lib.oracle_forward_history(self.dim, self.n3.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.h,
+                                        self.dt, self.nt, self.order, _dp(self.c), _dp(x), _dp(hist))
+        if rc != 0:
+            raise ValueError(f"oracle_forward_history failed ({rc})")
+        return hist

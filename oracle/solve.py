@@ -1,0 +1,60 @@
+"""FP64 conjugate-gradient solve of the regularised PAT problem (test
+infrastructure only).
+
+Paper Eq. (linear_minimization): (E_s* K* K + alpha I) x = E_s* K* p.  The
+same minimiser is reached on the symmetric positive definite system in wavelet
+coefficients
+
+    (E_s* K* K E_s + alpha I) u = E_s* K* y,   x = E_s u,
+
+because multiplying it by E_s gives (E_s E_s* K* K + alpha I)(E_s u) =
+E_s E_s* K* y, the paper's system with its covariance E_s E_s*, and E_s is
+invertible.  Plain CG from u0 (default 0) for a fixed number of iterations;
+each iteration costs one K and one K*, plus one K* for the right-hand side
+(the 1 + 2k count of Sec. 5).  alpha is absolute.
+"""
+import numpy as np
+
+
+class Breakdown(RuntimeError):
+    pass
+
+
+def normal_op(wave, wav, s, alpha):
+    """p -> E_s* K* K E_s p + alpha p."""
+    def H(p):
+        return wav.EsT(wave.adjoint(wave.forward(wav.Es(p, s))), s).ravel() + alpha * p
+    return H
+
+
+def rhs(wave, wav, y, s):
+    """b = E_s* K* y."""
+    return wav.EsT(wave.adjoint(y), s).ravel()
+
+
+def cg(wave, wav, y, alpha, s, iters, u0=None):
+    """Returns (u, x, log) with log[k] = (rr_k, pq_k, a_k) per iteration."""
+    H = normal_op(wave, wav, s, alpha)
+    b = rhs(wave, wav, y, s)
+    if u0 is None:
+        u = np.zeros_like(b)
+        r = b.copy()
+    else:
+        u = np.asarray(u0, dtype=np.float64).ravel().copy()
+        r = b - H(u)
+    p = r.copy()
+    rr = float(r @ r)
+    log = []
+    for _ in range(iters):
+        q = H(p)
+        pq = float(p @ q)
+        if not np.isfinite(pq) or pq <= 0.0:
+            raise Breakdown(f"p.q = {pq}")
+        a = rr / pq
+        u += a * p
+        r -= a * q
+        rr_new = float(r @ r)
+        log.append((rr, pq, a))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return u, wav.Es(u, s), np.array(log)
