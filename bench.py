@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the wavelet-Sobolev PAT reconstruction on GB300.
+
+One step = one full reconstruction of the 2D 512 x 512 workload: smooth
+random speed of sound in [1400, 1600] m/s, order-8 staggered stencil, 1500
+time samples, 512 sensors on a circle, db4 with 5 levels, and 100 CG
+iterations on (E_s* K* K E_s + alpha I) u = E_s* K* y (plus the right-hand
+side's K* and the final E_s u).  Steps cycle through s in {1, 2} x alpha in
+{1e-3, 1e-2} (alpha relative to lambda_max of E_s* K* K E_s, estimated by
+power iteration before timing).  Metric: reconstruction iterations per second
+(one K + one K* per iteration), whole job.
+
+With N > 1 (torchrun) every rank solves its own independently seeded
+instance (weak scaling, no data-path collective).
+
+--impl reference runs the FP64 CPU oracle (the reference arm of this
+build): each step is one oracle CG iteration of the same workload.
+"""
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "reconstruction iterations/sec (K+K* pairs)"
+UNIT = "iterations/s"
+WORKLOAD = "vessels"
+WORKLOAD_DESC = ("2D 512x512, c in [1400,1600] m/s (Gaussian-filtered noise), order-8 staggered FDTD, 1500 steps, "
+                 "512 sensors on a circle, p0 = 4 blobs + 6 Bezier vessels, 2% noise, db4 5 levels, "
+                 "s in {1,2} x alpha in {1e-3,1e-2}, 100 CG iterations, FP32 fields + FP64 CG scalars")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the persistent wave kernel from the committed
+    ncu summary, or None if absent or taken on a different kernel source."""
+    src = hashlib.sha256()
+    for f in ("wave2d_persist.cu", "stencil.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_02401_gb300", "csrc", f), "rb") as fh:
+            src.update(fh.read())
+    digest = src.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "wave2d_persist_512_o8.txt")
+    if not os.path.exists(path):
+        return None, digest
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != digest:
+        return None, digest
+    try:
+        return float(vals["dram_bytes_per_launch"]), digest
+    except (KeyError, ValueError):
+        return None, digest
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu_index = gpu_index
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            text, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            text = ""
+        sm, mx, reasons = [], [], set()
+        for row in csv.reader(io.StringIO(text)):
+            if len(row) < len(self.FIELDS):
+                continue
+            row = [r.strip() for r in row]
+            try:
+                sm.append(float(row[1].split()[0]))
+                mx.append(float(row[2].split()[0]))
+            except ValueError:
+                continue
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                               row[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(use_cuda):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    if use_cuda:
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, use_cuda):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local < len(parts) and parts[local].strip().isdigit():
+            return int(parts[local])
+    return local
+
+
+def cpu_baseline(w, iters_sample):
+    """The FP64 oracle, as it stands, on the host cores: `iters_sample` CG
+    iterations (one K, one K*, E_s, E_s* each) of the same workload."""
+    import oracle
+    wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
+    wav = oracle.Wavelet(w.shape, w.family, w.levels)
+    rng = np.random.default_rng(0)
+    y = rng.standard_normal((w.ns, w.nt))
+    t0 = time.perf_counter()
+    oracle.cg(wave, wav, y, 1e-3, 1.0, iters_sample)
+    dt = time.perf_counter() - t0
+    # a solve of k iterations costs 1 + 2k wave solves; count iterations as (2k+1)/2 pairs
+    pairs = (2 * iters_sample + 1) / 2.0
+    return {"value": pairs / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"oracle FP64 CG, {iters_sample} iterations (+ right-hand side) of the full 512x512 workload; "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed per step on one CG iteration."""
+    import synth
+    import oracle
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = synth.workload(WORKLOAD)
+    wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
+    wav = oracle.Wavelet(w.shape, w.family, w.levels)
+    H = oracle.normal_op(wave, wav, 1.0, 1e-3)
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(w.N)
+    for _ in range(args.warmup):
+        H(p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q = H(p)
+        a = float(p @ p) / float(p @ q)
+        p = p - a * q  # the CG vector work of one iteration is negligible beside H
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "step": "one oracle CG iteration (K + K* + E_s + E_s*)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed oracle CG iterations after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def lambda_max(plan, s, iters=20, seed=0):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    v = torch.randn(plan.N, device="cuda", generator=g)
+    v /= v.norm()
+    lam = 0.0
+    for _ in range(iters):
+        hv = plan.EsT(plan.adjoint(plan.forward(plan.Es(v, s))), s)
+        lam = float(hv.norm())
+        v = hv / lam
+    return lam
+
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_2507_02401_gb300 import Plan, _lib
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    rank, world, local = dist_setup(True)
+    w = synth.workload(WORKLOAD, seed=1001 + rank)
+    if args.iters:
+        w.iters = args.iters
+    c = w.c if np.ndim(w.c) == 0 else w.c_array()
+    plan = Plan(w.shape, w.h, w.dt, w.nt, w.order, c, w.sensors, w.family, w.levels)
+    stream = torch.cuda.current_stream()
+    x_true = torch.as_tensor(w.x_true, dtype=torch.float32, device="cuda")
+    y_clean = plan.forward(x_true).cpu().numpy()
+    y_np = synth.add_noise(y_clean, w.noise, np.random.default_rng(1234 + rank)).astype(np.float32)
+    y = torch.as_tensor(y_np, device="cuda")
+    combos = []
+    for s in w.s:
+        lam = lambda_max(plan, s)
+        for a in w.alpha:
+            combos.append((s, a * lam))
+    u = torch.empty(plan.N, device="cuda")
+    x = torch.empty(w.shape, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+
+    def solve(k, yy=y, xx=x, uu=u):
+        s, alpha = combos[k % len(combos)]
+        _lib.pat_solve(plan.handle, yy, alpha, s, w.iters, None, uu, xx, None, stream)
+
+    for k in range(args.warmup):
+        solve(k)
+    torch.cuda.synchronize()
+    assert plan.check() == 0, _lib.pat_last_error()
+
+    sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
+    _lib.pat_plan_profile(plan.handle, 1)
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps (inside the timed region; ~0.01% of a step)
+        solve(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, True)
+    kernels, wave_calls, wave_ms, points = _lib.pat_plan_profile_read(plan.handle)
+    _lib.pat_plan_profile(plan.handle, 0)
+    status = plan.check()
+    assert status == 0, f"device status {status}: {_lib.pat_last_error()}"
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    y_host = torch.empty((w.ns, w.nt), dtype=torch.float32, pin_memory=True)
+    y_host.copy_(torch.as_tensor(y_np))
+    x_host = torch.empty(w.shape, dtype=torch.float32, pin_memory=True)
+    yh, xh = y_host.numpy(), x_host.numpy()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s, alpha = combos[k % len(combos)]
+        _lib.pat_solve(plan.handle, yh, alpha, s, w.iters, None, None, xh, None, stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, True)
+    barrier(world)
+
+    iters_total = world * args.steps * w.iters
+    value = iters_total / (t_ms / 1e3)
+    bytes_per_pt = 16 if plan_varc(w) else 12
+    per_launch_bytes = bytes_per_pt * w.N * (w.nt - 1)
+    achieved = per_launch_bytes * wave_calls / (wave_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
+    peak, peak_kind = peaks()
+    traffic, digest = kernel_traffic()
+    engine = {1: "persistent", 2: "step"}.get(plan.path, "?")
+    gpts = world * args.steps * (2 * w.iters + 1) * (w.nt - 1) * w.N / (t_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "engine": engine, "iters_per_step": w.iters,
+                   "l2": "256 MiB buffer written before every step (inside the timed region)",
+                   "parallelism": f"replicas x{world} (independent instances per rank)"},
+        "gpoint_updates_per_s": gpts,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": f"wave2d_persist_kernel<R=7,varc> ({engine} engine)",
+                     "algorithmic_bytes_per_point_update": bytes_per_pt,
+                     "launch_ms": wave_ms / max(wave_calls, 1), "launches_timed": wave_calls,
+                     "source_sha256_16": digest},
+        "e2e": {"value": iters_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_np.nbytes),
+                "d2h_bytes_per_step": int(w.N * 4)},
+        "gpu_launches": int(kernels + args.steps),  # library kernels + one L2 flush per step
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_iters)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def plan_varc(w):
+    return np.ndim(w.c) != 0 and float(np.max(w.c)) != float(np.min(w.c))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=0, help="override CG iterations per step")
+    ap.add_argument("--cpu-iters", type=int, default=4, help="oracle CG iterations in the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

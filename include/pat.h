@@ -1,0 +1,207 @@
+/*
+ * pat.h — C ABI of the GB300 photoacoustic reconstruction library.
+ *
+ * The library solves the wavelet-Sobolev / Matern regularised PAT problem of
+ * Kultima, Ramlau, Sahlstrom, Tarvainen (arXiv 2507.02401):
+ *
+ *     min_u  1/2 || K E_s u - y ||^2 + alpha/2 || u ||^2 ,     x = E_s u,
+ *
+ * i.e. the normal equations (E_s* K* K E_s + alpha I) u = E_s* K* y, which
+ * are the paper's Eq. (linear_minimization) written in wavelet coefficients
+ * (multiply by E_s to recover (E_s E_s* K* K + alpha I) x = E_s E_s* K* y).
+ *
+ *   K    photoacoustic forward map (Sec. 2.2): initial pressure p0 on an
+ *        n^d grid -> pressure at Ns point sensors for nt time samples, from
+ *        the wave IVP of Eq. (wave_equation) discretised as a staggered
+ *        leapfrog of spatial order 2M (2, 4, 6, 8), pressure zero outside
+ *        the grid, p_t(0) = 0.
+ *   K*   its exact discrete adjoint (transpose, Euclidean inner products).
+ *   E_s  wavelet form of the Sobolev embedding (Sec. 4, Prop. 4.2): periodic
+ *        orthonormal Daubechies synthesis W^T after scaling the level-i detail
+ *        block by 2^{-s(m-i+o)} (i = 1 finest, m levels, o = level offset);
+ *        E_s* = S_s W is its adjoint, and E_s E_s* = W^T S_s^2 W is the
+ *        paper's operator W^{-1}(D W .) of Sec. 4.
+ *
+ * Conventions for every call:
+ *   - Grids are row-major with x fastest: cell (x, y[, z]) at
+ *     (z*ny + y)*nx + x, cell centre at (x*h, y*h, z*h).
+ *   - Sensor data y are sensor-major: y[s*nt + t], t = 0 .. nt-1, t = 0 being
+ *     the initial pressure itself.
+ *   - Coefficient vectors u have N = n^d entries laid out as
+ *     [cA_m, bands_m, bands_{m-1}, ..., bands_1], every band row-major;
+ *     2D bands in the paper's order (H = x low/y high, V = x high/y low,
+ *     D = both high), 3D bands in binary (z,y,x) order 001 .. 111 (1 = high).
+ *   - Array pointers may be device pointers (fast path) or host pointers
+ *     (pageable or pinned); host arrays are staged through plan-owned device
+ *     buffers inside the call, which then returns only after the result is
+ *     back on the host.  The caller owns every array it passes.
+ *   - Calls with device pointers are asynchronous on `stream` (a
+ *     cudaStream_t, NULL = legacy default stream).  Argument errors are
+ *     returned immediately; device-side conditions (a timed-out wait inside a
+ *     persistent kernel, a CG breakdown) are recorded in the plan and
+ *     returned by pat_plan_check().
+ *   - Calls on one plan must not overlap in time (they share the plan's
+ *     workspace); different plans are independent.
+ *   - Nothing aborts the process: errors are status codes, with a message in
+ *     pat_last_error().
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pat_plan pat_plan;
+
+typedef enum {
+  PAT_OK = 0,
+  PAT_ERR_INVALID = 1,   /* bad argument (sizes, order, sensor outside grid, NaN, ...) */
+  PAT_ERR_CFL = 2,       /* c_max dt / h above the stability limit of the chosen order */
+  PAT_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  PAT_ERR_OOM = 4,       /* device allocation failed */
+  PAT_ERR_TIMEOUT = 5,   /* a bounded wait in a persistent kernel ran out */
+  PAT_ERR_BREAKDOWN = 6  /* CG met p.q <= 0 or a non-finite scalar; last iterate kept */
+} pat_status;
+
+/* Grid: dim = 2 or 3; n = {nx, ny, nz} (nz ignored for dim 2); spacing h [m]. */
+typedef struct {
+  int dim;
+  int n[3];
+  double h;
+} pat_grid;
+
+/* Wavelet: family = number of vanishing moments (1 = Haar, 2 = db2, 4 = db4);
+ * levels m >= 1 with every n[i] divisible by 2^m; level_offset o >= 0
+ * (0 = the paper's inline weight 2^{-2s(m-i)} for E_s E_s*). */
+typedef struct {
+  int family;
+  int levels;
+  int level_offset;
+} pat_wavelet;
+
+/*
+ * pat_plan_create — validate a problem and build its device constants.
+ * Paper Sec. 2 (Eq. wave_equation, the sensor map K) and Sec. 4 (W, D).
+ *   grid     grid description (host).
+ *   c        host array of N speeds of sound [m/s] (double), or NULL to use
+ *            the constant c0.  Must be finite and > 0.
+ *   sensors  host array ns x dim of sensor coordinates (x, y[, z]) [m]; each
+ *            must lie in [0, (n_i - 1) h] (bilinear/trilinear sampling).
+ *   dt, nt   time step [s] and number of samples (nt >= 1).
+ *   order    spatial order 2, 4, 6 or 8 of the staggered scheme.  The plan
+ *            is rejected with PAT_ERR_CFL when c_max dt / h exceeds
+ *            1 / (sqrt(dim) * sum_k |c_k|) for the order's staggered weights.
+ *   wavelet  wavelet description (host).
+ *   stream   stream for the set-up copies (the call synchronises it).
+ *   out      receives the plan; owns all device memory it needs (device
+ *            constants and the workspace of every call).
+ */
+pat_status pat_plan_create(const pat_grid* grid, const double* c, double c0, const double* sensors, int ns,
+                           double dt, int nt, int order, const pat_wavelet* wavelet, void* stream,
+                           pat_plan** out);
+
+/* Frees a plan and all device memory it owns.  NULL is ignored. */
+void pat_plan_destroy(pat_plan* plan);
+
+/* Sizes of a plan: number of cells N (= coefficient count), sensors, samples. */
+pat_status pat_plan_info(const pat_plan* plan, long long* n_cells, int* ns, int* nt);
+
+/*
+ * pat_forward — y = K x.  Paper Sec. 2.2 (K: p0 -> [p(r_i, t_j)]).
+ *   x  N floats (initial pressure).   y  ns*nt floats (sensor-major).
+ */
+pat_status pat_forward(pat_plan* plan, const float* x, float* y, void* stream);
+
+/*
+ * pat_adjoint — x = K* y, the exact transpose of pat_forward (reverse-time
+ * recurrence with transposed sensor injection).  Paper Sec. 4 (K* needed by
+ * the matrix-free solver).   y  ns*nt floats.   x  N floats.
+ */
+pat_status pat_adjoint(pat_plan* plan, const float* y, float* x, void* stream);
+
+/*
+ * pat_Es — x = E_s u = W^T S_s u (coefficients -> image).  Paper Sec. 4,
+ * Prop. 4.2 (diagonal scaling of the wavelet coefficients).
+ *   s  smoothness index (any real; s = 0 gives W^T).   u, x  N floats.
+ */
+pat_status pat_Es(pat_plan* plan, double s, const float* u, float* x, void* stream);
+
+/* pat_EsT — u = E_s* x = S_s W x (image -> coefficients).  Paper Sec. 4. */
+pat_status pat_EsT(pat_plan* plan, double s, const float* x, float* u, void* stream);
+
+/*
+ * pat_solve — CG on (E_s* K* K E_s + alpha I) u = E_s* K* y for `iters`
+ * iterations (paper Eq. linear_minimization, Sec. 4 "GMRES or CG"; each
+ * iteration costs one K and one K*, plus one K* for the right-hand side).
+ * Vectors are FP32; inner products, step lengths and the residual norm are
+ * FP64 on the device; no host synchronisation inside.
+ *   y      ns*nt floats (data).         alpha  absolute regularisation > 0.
+ *   s      smoothness index.            iters  >= 0.
+ *   u0     N floats initial coefficients, or NULL for u0 = 0.
+ *   u      N floats, final coefficients (may be NULL).
+ *   x      N floats, final image E_s u (may be NULL).
+ *   log    NULL or a DEVICE array of iters*3 doubles receiving, per
+ *          iteration k, (r_k.r_k, p_k.q_k, a_k).
+ * A breakdown keeps the last iterate and is reported by pat_plan_check().
+ */
+pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int iters, const float* u0, float* u,
+                     float* x, double* log, void* stream);
+
+/*
+ * pat_solve_batched — B independent pat_solve problems (each with its own
+ * plan, data, alpha and s; a common iteration count) advanced together.
+ *   plans, ys, xs   host arrays of B plan / device-array pointers (xs[i]
+ *                   receives E_s u of instance i).
+ *   alphas, ss      host arrays of B doubles.
+ *   per_inst        NULL or host array of B statuses; filled after the call
+ *                   synchronises `stream` (the call is synchronous).
+ */
+pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* ys, const double* alphas,
+                             const double* ss, int iters, float* const* xs, pat_status* per_inst, void* stream);
+
+/*
+ * pat_plan_check — synchronises `stream`, returns and clears the plan's
+ * device-side status (PAT_OK, PAT_ERR_TIMEOUT or PAT_ERR_BREAKDOWN), or
+ * PAT_ERR_CUDA if the stream reports an error.
+ */
+pat_status pat_plan_check(pat_plan* plan, void* stream);
+
+/*
+ * Wave engine of a plan (tuning and testing):
+ *   PAT_PATH_AUTO        default choice (persistent when available)
+ *   PAT_PATH_PERSISTENT  2D only: one cooperative launch per K / K* with the
+ *                        wavefield kept on chip; available when every 64 x 32
+ *                        tile of the grid can be resident at once
+ *   PAT_PATH_STEP        one launch per time step (any grid; 3D always)
+ * Both engines compute the same operators (to FP32 rounding).
+ */
+typedef enum { PAT_PATH_AUTO = 0, PAT_PATH_PERSISTENT = 1, PAT_PATH_STEP = 2 } pat_path;
+pat_status pat_plan_set_path(pat_plan* plan, int path);
+pat_status pat_plan_get_path(const pat_plan* plan, int* path);
+
+/* Bound (nanoseconds, default 2e9) on any single inter-tile wait inside the
+ * persistent engine; when it runs out the call ends early and
+ * pat_plan_check() reports PAT_ERR_TIMEOUT. */
+pat_status pat_plan_set_timeout(pat_plan* plan, long long timeout_ns);
+
+/*
+ * Measurement hooks.  While enabled, every wave-engine application (one K or
+ * one K*) is bracketed by CUDA events recorded on the stream it runs on, and
+ * every kernel the plan launches is counted.  pat_plan_profile(plan, 1)
+ * clears the counters; pat_plan_profile_read synchronises on the recorded
+ * events and returns: kernels launched, wave applications timed, their
+ * summed device time [ms] and the point-updates they made (cells x steps).
+ */
+pat_status pat_plan_profile(pat_plan* plan, int enable);
+pat_status pat_plan_profile_read(pat_plan* plan, long long* kernels, int* wave_calls, double* wave_ms,
+                                 long long* point_updates);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* pat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAT_H */

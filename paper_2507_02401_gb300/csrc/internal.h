@@ -1,0 +1,142 @@
+// Internal declarations of the GB300 PAT library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pat.h"
+
+namespace pat {
+
+constexpr int kMaxR = 7;       // composed stencil radius of order 8
+constexpr int kMaxTaps = 8;    // db4 filter length
+constexpr int kMaxLevels = 20;
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+pat_status cuda_fail(cudaError_t e, const char* what);
+
+#define PAT_TRY_CUDA(expr)                                       \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return ::pat::cuda_fail(_e, #expr);   \
+  } while (0)
+
+#define PAT_TRY(expr)                       \
+  do {                                      \
+    pat_status _s = (expr);                 \
+    if (_s != PAT_OK) return _s;            \
+  } while (0)
+
+// ------------------------------------------------------- device structs
+// One sensor's bilinear sampling entry inside a persistent 2D tile.
+struct SampEntry {
+  int sensor;
+  short lx, ly;  // base cell in tile-local coordinates
+  float w[4];    // weights of (lx,ly), (lx+1,ly), (lx,ly+1), (lx+1,ly+1)
+};
+
+// One injected cell inside a persistent 2D tile: entries [beg, end) of the
+// plan's (sensor, weight) list, summed in that order.
+struct InjCell {
+  int local;  // ly * TX + lx
+  int beg, end;
+};
+
+// Arguments of the persistent 2D wave kernel.
+struct Persist2DArgs {
+  int nx, ny, nt;
+  int tiles_x, tiles_y;
+  float w[kMaxR + 1];  // composed stencil weights, w[1..R]
+  float kappa0;        // (c dt / h)^2 when the medium is constant
+  const float* kappa;  // per-cell kappa, or nullptr
+  const float* in;     // forward: x (N);  adjoint: y (ns*nt)
+  float* out;          // forward: y;      adjoint: x
+  const int* tile_samp_ptr;
+  const SampEntry* samp;
+  const int* tile_inj_ptr;
+  const InjCell* inj;
+  const int* ent_sensor;
+  const float* ent_w;
+  float* xbuf;           // boundary strips, 2 slots per tile
+  int* flags;            // per-tile published state counter
+  unsigned* epoch;       // launch counter (device)
+  unsigned* done;        // CTAs finished in this launch
+  int* abort;            // set when any CTA gives up
+  int* status;           // sticky plan status
+  long long timeout_ns;  // bound on any single wait
+};
+
+// Arguments of the per-step kernels (2D tile kernel and 3D z-marching kernel).
+struct StepArgs {
+  int nx, ny, nz;
+  float w[kMaxR + 1];
+  float kappa0;
+  const float* kappa;  // or nullptr
+  const float* cur;    // P^n (forward) or Q^{n+1} (adjoint)
+  const float* prev;   // P^{n-1} or Q^{n+2}   (nullptr on the first step)
+  float* next;         // P^{n+1} or Q^n
+  float c_lap;         // coefficient of kappa*L (1, or 0.5 for the first/last step)
+  float c_cur;         // coefficient of the current field (2, or 1)
+  float c_prev;        // coefficient of the previous field (1, or 0)
+  // fused sampling of `cur` (forward): y[s*nt + t_sample] for s in [0, ns)
+  int ns, nt, t_sample;
+  const int* sens_cell;
+  const float* sens_w;
+  int corners;
+  float* y;
+};
+
+// ------------------------------------------------------------ launchers
+// wave2d_persist.cu
+bool persist2d_supported(int R, bool varc);
+int persist2d_tile_x();
+int persist2d_tile_y();
+size_t persist2d_smem_bytes(int R, bool adj);
+int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
+cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
+
+// wave_step.cu
+cudaError_t step2d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);
+cudaError_t step3d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);
+cudaError_t sample_launch(const float* P, int ns, int nt, int t, const int* cell, const float* w, int corners,
+                          float* y, cudaStream_t st);
+cudaError_t inject_launch(float* Q, int n_inj, const int* inj_cell, const int* inj_ptr, const int* ent_sensor,
+                          const float* ent_w, const float* r, int nt, int t, float scale, cudaStream_t st);
+cudaError_t fill_launch(float* p, long long n, float v, cudaStream_t st);
+cudaError_t copy_launch(float* dst, const float* src, long long n, cudaStream_t st);
+
+// dwt.cu
+cudaError_t dwt2d_analysis_level(const float* in, int nx, int ny, float* approx, float* bandH, float* bandV,
+                                 float* bandD, float wdet, const float* h, const float* g, int L, cudaStream_t st);
+cudaError_t dwt2d_synthesis_level(const float* approx, const float* bandH, const float* bandV, const float* bandD,
+                                  float wdet, int nx, int ny, float* out, const float* h, const float* g, int L,
+                                  cudaStream_t st);
+cudaError_t dwt1d_analysis_axis(const float* in, int n0, int n1, int n2, int axis, float* lo, float* hi, float wlo,
+                                float whi, const float* h, const float* g, int L, cudaStream_t st);
+cudaError_t dwt1d_synthesis_axis(const float* lo, const float* hi, float wlo, float whi, int n0, int n1, int n2,
+                                 int axis, float* out, const float* h, const float* g, int L, cudaStream_t st);
+cudaError_t scale_copy_launch(float* dst, const float* src, long long n, float w, cudaStream_t st);
+
+// cg.cu
+struct CgScalars {
+  double rr, pq, a, rr_new, beta;
+  int stopped;
+  int iter;
+};
+int cg_grid_blocks();
+cudaError_t cg_init_launch(const float* b, float* r, float* p, float* u, long long n, bool zero_u, double* partials,
+                           unsigned* counter, CgScalars* sc, cudaStream_t st);
+cudaError_t cg_sub_launch(float* r, const float* q, long long n, cudaStream_t st);  // r -= q
+cudaError_t cg_pq_launch(float* q, const float* p, double alpha, long long n, double* partials, unsigned* counter,
+                         CgScalars* sc, cudaStream_t st);
+cudaError_t cg_update_launch(float* u, float* r, const float* p, const float* q, long long n, double* partials,
+                             unsigned* counter, CgScalars* sc, double* log, int* status, cudaStream_t st);
+cudaError_t cg_direction_launch(float* p, const float* r, long long n, const CgScalars* sc, cudaStream_t st);
+cudaError_t cg_rr_launch(const float* r, float* p, long long n, double* partials, unsigned* counter, CgScalars* sc,
+                         cudaStream_t st);  // p = r, rr = r.r
+
+}  // namespace pat

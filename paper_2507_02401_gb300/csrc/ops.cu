@@ -1,0 +1,534 @@
+// Operators and solver behind the C ABI: K, K*, E_s, E_s*, CG.
+#include <cmath>
+#include <cstring>
+
+#include "plan.h"
+
+namespace pat {
+
+// ------------------------------------------------------------------- K, K*
+static Persist2DArgs persist_args(pat_plan* p) {
+  Persist2DArgs a{};
+  a.nx = p->n[0];
+  a.ny = p->n[1];
+  a.nt = p->nt;
+  a.tiles_x = p->tiles_x;
+  a.tiles_y = p->tiles_y;
+  for (int m = 0; m <= kMaxR; ++m) a.w[m] = p->w[m];
+  a.kappa0 = p->kappa0;
+  a.kappa = p->varc ? p->d_kappa : nullptr;
+  a.tile_samp_ptr = p->d_tile_samp_ptr;
+  a.samp = p->d_samp;
+  a.tile_inj_ptr = p->d_tile_inj_ptr;
+  a.inj = p->d_tinj;
+  a.ent_sensor = p->d_ent_sensor;
+  a.ent_w = p->d_ent_w;
+  a.xbuf = p->d_xbuf;
+  a.flags = p->d_flags;
+  a.epoch = p->d_epoch;
+  a.done = p->d_done;
+  a.abort = p->d_abort;
+  a.status = p->d_status;
+  a.timeout_ns = p->timeout_ns;
+  return a;
+}
+
+static StepArgs step_args(pat_plan* p) {
+  StepArgs a{};
+  a.nx = p->n[0];
+  a.ny = p->n[1];
+  a.nz = p->n[2];
+  for (int m = 0; m <= kMaxR; ++m) a.w[m] = p->w[m];
+  a.kappa0 = p->kappa0;
+  a.kappa = p->varc ? p->d_kappa : nullptr;
+  a.ns = p->ns;
+  a.nt = p->nt;
+  a.sens_cell = p->d_sens_cell;
+  a.sens_w = p->d_sens_w;
+  a.corners = p->corners;
+  return a;
+}
+
+static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t st) {
+  // sample separately when the step grid has fewer threads than sensors
+  float* y = a.y;
+  cudaError_t e;
+  if (p->dim == 2) {
+    const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
+    if (y && a.ns > nthr) a.y = nullptr;
+    e = step2d_launch(p->R, adj, a, st);
+  } else {
+    const long long nthr =
+        (long long)((p->n[0] + 31) / 32) * ((p->n[1] + 15) / 16) * ((p->n[2] + 31) / 32) * 128;
+    if (y && a.ns > nthr) a.y = nullptr;
+    e = step3d_launch(p->R, adj, a, st);
+  }
+  if (e == cudaSuccess && y && !a.y)
+    e = sample_launch(a.cur, p->ns, p->nt, a.t_sample, p->d_sens_cell, p->d_sens_w, p->corners, y, st);
+  a.y = y;
+  return e;
+}
+
+static pat_status wave_forward_impl(pat_plan* p, const float* x, float* y, cudaStream_t st) {
+  if (p->path == PAT_PATH_PERSISTENT) {
+    Persist2DArgs a = persist_args(p);
+    a.in = x;
+    a.out = y;
+    PAT_TRY_CUDA(persist2d_launch(p->R, false, p->varc, a, p->ntiles, st));
+    return PAT_OK;
+  }
+  const int nt = p->nt;
+  if (nt == 1) {
+    PAT_TRY_CUDA(sample_launch(x, p->ns, nt, 0, p->d_sens_cell, p->d_sens_w, p->corners, y, st));
+    return PAT_OK;
+  }
+  // F_0 = x, F_n = wv[(n-1) % 3] for n >= 1; step n makes F_{n+1} and samples F_n
+  StepArgs a = step_args(p);
+  a.y = y;
+  for (int n = 0; n < nt - 1; ++n) {
+    a.cur = (n == 0) ? x : p->d_wv[(n - 1) % 3];
+    a.prev = (n == 0) ? nullptr : (n == 1 ? x : p->d_wv[(n - 2) % 3]);
+    a.next = p->d_wv[n % 3];
+    a.c_cur = (n == 0) ? 1.f : 2.f;
+    a.c_prev = (n == 0) ? 0.f : 1.f;
+    a.c_lap = (n == 0) ? 0.5f : 1.f;
+    a.t_sample = n;
+    PAT_TRY_CUDA(step_launch(p, false, a, st));
+  }
+  PAT_TRY_CUDA(sample_launch(p->d_wv[(nt - 2) % 3], p->ns, nt, nt - 1, p->d_sens_cell, p->d_sens_w, p->corners, y, st));
+  return PAT_OK;
+}
+
+static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaStream_t st) {
+  if (p->path == PAT_PATH_PERSISTENT) {
+    Persist2DArgs a = persist_args(p);
+    a.in = y;
+    a.out = x;
+    PAT_TRY_CUDA(persist2d_launch(p->R, true, p->varc, a, p->ntiles, st));
+    return PAT_OK;
+  }
+  const int nt = p->nt;
+  auto inject = [&](float* Q, int t) {
+    return inject_launch(Q, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, y, nt, t, 1.f, st);
+  };
+  if (nt == 1) {
+    PAT_TRY_CUDA(fill_launch(x, p->N, 0.f, st));
+    PAT_TRY_CUDA(inject(x, 0));
+    return PAT_OK;
+  }
+  // Q^m lives in wv[(nt-1-m) % 3]
+  auto Qbuf = [&](int m) { return p->d_wv[(nt - 1 - m) % 3]; };
+  PAT_TRY_CUDA(fill_launch(Qbuf(nt - 1), p->N, 0.f, st));
+  PAT_TRY_CUDA(inject(Qbuf(nt - 1), nt - 1));
+  StepArgs a = step_args(p);
+  a.y = nullptr;
+  for (int m = nt - 2; m >= 1; --m) {
+    a.cur = Qbuf(m + 1);
+    a.prev = (m + 2 <= nt - 1) ? Qbuf(m + 2) : nullptr;
+    a.next = Qbuf(m);
+    a.c_cur = 2.f;
+    a.c_prev = 1.f;
+    a.c_lap = 1.f;
+    PAT_TRY_CUDA(step_launch(p, true, a, st));
+    PAT_TRY_CUDA(inject(Qbuf(m), m));
+  }
+  a.cur = Qbuf(1);
+  a.prev = (nt >= 3) ? Qbuf(2) : nullptr;
+  a.next = x;
+  a.c_cur = 1.f;
+  a.c_prev = 1.f;
+  a.c_lap = 0.5f;
+  PAT_TRY_CUDA(step_launch(p, true, a, st));
+  PAT_TRY_CUDA(inject(x, 0));
+  return PAT_OK;
+}
+
+// ------------------------------------------------------- measurement hooks
+static pat_status prof_mark(pat_plan* p, cudaStream_t st) {
+  if ((int)p->prof_ev.size() <= p->prof_used) {
+    cudaEvent_t e;
+    PAT_TRY_CUDA(cudaEventCreate(&e));
+    p->prof_ev.push_back(e);
+  }
+  PAT_TRY_CUDA(cudaEventRecord(p->prof_ev[p->prof_used++], st));
+  return PAT_OK;
+}
+
+static long long wave_kernels(const pat_plan* p, bool adj) {
+  if (p->path == PAT_PATH_PERSISTENT) return 1;
+  const long long nt = p->nt;
+  if (nt == 1) return adj ? 2 : 1;
+  if (!adj) return nt;         // nt-1 steps + final sample
+  return 2 + 2 * (nt - 2) + 2;  // fill+inject, (step+inject) x (nt-2), final step+inject
+}
+
+pat_status wave_forward(pat_plan* p, const float* x, float* y, cudaStream_t st) {
+  if (p->prof_on) PAT_TRY(prof_mark(p, st));
+  PAT_TRY(wave_forward_impl(p, x, y, st));
+  if (p->prof_on) {
+    PAT_TRY(prof_mark(p, st));
+    p->prof_kernels += wave_kernels(p, false);
+    p->prof_points += p->N * (long long)(p->nt - 1);
+  }
+  return PAT_OK;
+}
+
+pat_status wave_adjoint(pat_plan* p, const float* y, float* x, cudaStream_t st) {
+  if (p->prof_on) PAT_TRY(prof_mark(p, st));
+  PAT_TRY(wave_adjoint_impl(p, y, x, st));
+  if (p->prof_on) {
+    PAT_TRY(prof_mark(p, st));
+    p->prof_kernels += wave_kernels(p, true);
+    p->prof_points += p->N * (long long)(p->nt - 1);
+  }
+  return PAT_OK;
+}
+
+static void count_kernels(pat_plan* p, long long k) {
+  if (p->prof_on) p->prof_kernels += k;
+}
+
+// ------------------------------------------------------------- E_s, E_s*
+static float level_weight(const pat_plan* p, int i, double s) {
+  return (float)std::pow(2.0, -s * (double)(p->levels - i + p->level_offset));
+}
+
+// offset of band b (0-based) of level i in the coefficient vector
+static long long band_offset(const pat_plan* p, int i, int b) {
+  const int d = p->dim;
+  const int nb = (1 << d) - 1;
+  long long off = p->N >> (d * p->levels);
+  for (int j = p->levels; j > i; --j) off += (long long)nb * (p->N >> (d * j));
+  return off + (long long)b * (p->N >> (d * i));
+}
+
+pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream_t st) {
+  const int m = p->levels;
+  float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
+  const float* in = x;
+  for (int i = 1; i <= m; ++i) {
+    const int ex = p->n[0] >> (i - 1), ey = p->n[1] >> (i - 1), ez = p->n[2] >> (i - 1);
+    float* approx = (i == m) ? u : tmp[i & 1];
+    const float wd = level_weight(p, i, s);
+    if (p->dim == 2) {
+      PAT_TRY_CUDA(dwt2d_analysis_level(in, ex, ey, approx, u + band_offset(p, i, 0), u + band_offset(p, i, 1),
+                                        u + band_offset(p, i, 2), wd, p->hf, p->gf, p->L, st));
+    } else {
+      const long long ni = (long long)ex * ey * ez;
+      float* T1 = p->d_dwt_t1;  // x-pass: lo | hi (ni/2 each)
+      float* T2 = p->d_dwt_t2;  // y-pass: 4 quarters, index xb | yb<<1
+      PAT_TRY_CUDA(dwt1d_analysis_axis(in, ex, ey, ez, 0, T1, T1 + ni / 2, 1.f, 1.f, p->hf, p->gf, p->L, st));
+      for (int xb = 0; xb < 2; ++xb)
+        PAT_TRY_CUDA(dwt1d_analysis_axis(T1 + xb * (ni / 2), ex / 2, ey, ez, 1, T2 + (xb | 0) * (ni / 4),
+                                         T2 + (xb | 2) * (ni / 4), 1.f, 1.f, p->hf, p->gf, p->L, st));
+      for (int q = 0; q < 4; ++q) {
+        float* lo = (q == 0) ? approx : u + band_offset(p, i, q - 1);
+        float* hi = u + band_offset(p, i, (q | 4) - 1);
+        PAT_TRY_CUDA(dwt1d_analysis_axis(T2 + q * (ni / 4), ex / 2, ey / 2, ez, 2, lo, hi, q == 0 ? 1.f : wd, wd,
+                                         p->hf, p->gf, p->L, st));
+      }
+    }
+    in = approx;
+  }
+  count_kernels(p, (long long)m * (p->dim == 2 ? 1 : 7));
+  return PAT_OK;
+}
+
+pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_t st) {
+  const int m = p->levels;
+  float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
+  const float* approx = u;
+  for (int i = m; i >= 1; --i) {
+    const int ex = p->n[0] >> (i - 1), ey = p->n[1] >> (i - 1), ez = p->n[2] >> (i - 1);
+    float* out = (i == 1) ? x : tmp[i & 1];
+    const float wd = level_weight(p, i, s);
+    if (p->dim == 2) {
+      PAT_TRY_CUDA(dwt2d_synthesis_level(approx, u + band_offset(p, i, 0), u + band_offset(p, i, 1),
+                                         u + band_offset(p, i, 2), wd, ex, ey, out, p->hf, p->gf, p->L, st));
+    } else {
+      const long long ni = (long long)ex * ey * ez;
+      float* T1 = p->d_dwt_t1;
+      float* T2 = p->d_dwt_t2;
+      for (int q = 0; q < 4; ++q) {  // z: (code q, code q|4) -> T2 quarter q
+        const float* lo = (q == 0) ? approx : u + band_offset(p, i, q - 1);
+        const float* hi = u + band_offset(p, i, (q | 4) - 1);
+        PAT_TRY_CUDA(dwt1d_synthesis_axis(lo, hi, q == 0 ? 1.f : wd, wd, ex / 2, ey / 2, ez / 2, 2,
+                                          T2 + q * (ni / 4), p->hf, p->gf, p->L, st));
+      }
+      for (int xb = 0; xb < 2; ++xb)  // y: (xb, xb|2) -> T1 half xb
+        PAT_TRY_CUDA(dwt1d_synthesis_axis(T2 + xb * (ni / 4), T2 + (xb | 2) * (ni / 4), 1.f, 1.f, ex / 2, ey / 2, ez,
+                                          1, T1 + xb * (ni / 2), p->hf, p->gf, p->L, st));
+      PAT_TRY_CUDA(dwt1d_synthesis_axis(T1, T1 + ni / 2, 1.f, 1.f, ex / 2, ey, ez, 0, out, p->hf, p->gf, p->L, st));
+    }
+    approx = out;
+  }
+  count_kernels(p, (long long)m * (p->dim == 2 ? 1 : 7));
+  return PAT_OK;
+}
+
+// --------------------------------------------------------------------- CG
+static pat_status apply_normal(pat_plan* p, double s, const float* v, float* out, cudaStream_t st) {
+  // out = E_s* K* K E_s v   (alpha v is added by the fused dot kernel)
+  PAT_TRY(apply_Es(p, s, v, p->d_img, st));
+  PAT_TRY(wave_forward(p, p->d_img, p->d_ybuf, st));
+  PAT_TRY(wave_adjoint(p, p->d_ybuf, p->d_img, st));
+  PAT_TRY(apply_EsT(p, s, p->d_img, out, st));
+  return PAT_OK;
+}
+
+pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int iters, const float* u0, float* u,
+                        float* x, double* log, cudaStream_t st) {
+  const long long N = p->N;
+  float* uu = u ? u : p->d_u;
+  // r = b = E_s* K* y
+  PAT_TRY(wave_adjoint(p, y, p->d_img, st));
+  PAT_TRY(apply_EsT(p, s, p->d_img, p->d_r, st));
+  if (u0) {
+    if (u0 != uu) PAT_TRY_CUDA(cudaMemcpyAsync(uu, u0, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+    PAT_TRY(apply_normal(p, s, uu, p->d_q, st));
+    PAT_TRY_CUDA(cg_pq_launch(p->d_q, uu, alpha, N, p->d_partials, p->d_counter, p->d_sc, st));
+    PAT_TRY_CUDA(cg_sub_launch(p->d_r, p->d_q, N, st));
+    PAT_TRY_CUDA(cg_rr_launch(p->d_r, p->d_p, N, p->d_partials, p->d_counter, p->d_sc, st));
+    count_kernels(p, 3);
+  } else {
+    PAT_TRY_CUDA(cg_init_launch(p->d_r, p->d_r, p->d_p, uu, N, true, p->d_partials, p->d_counter, p->d_sc, st));
+    count_kernels(p, 1);
+  }
+  for (int k = 0; k < iters; ++k) {
+    PAT_TRY(apply_normal(p, s, p->d_p, p->d_q, st));
+    PAT_TRY_CUDA(cg_pq_launch(p->d_q, p->d_p, alpha, N, p->d_partials, p->d_counter, p->d_sc, st));
+    PAT_TRY_CUDA(cg_update_launch(uu, p->d_r, p->d_p, p->d_q, N, p->d_partials, p->d_counter, p->d_sc, log,
+                                  p->d_status, st));
+    PAT_TRY_CUDA(cg_direction_launch(p->d_p, p->d_r, N, p->d_sc, st));
+    count_kernels(p, 3);
+  }
+  if (x) PAT_TRY(apply_Es(p, s, uu, x, st));
+  return PAT_OK;
+}
+
+// ------------------------------------------------------- host staging
+static bool is_device_ptr(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static pat_status stage(pat_plan* p, int slot, size_t bytes, float** out) {
+  if (p->stage_bytes[slot] < bytes) {
+    if (p->d_stage[slot]) cudaFree(p->d_stage[slot]);
+    p->d_stage[slot] = nullptr;
+    p->stage_bytes[slot] = 0;
+    cudaError_t e = cudaMalloc(&p->d_stage[slot], bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->d_stage[slot] = nullptr;
+      return cuda_fail(e, "cudaMalloc(staging)");
+    }
+    p->stage_bytes[slot] = bytes;
+  }
+  *out = p->d_stage[slot];
+  return PAT_OK;
+}
+
+// Resolve an input array: device pointers pass through, host arrays are copied in.
+static pat_status in_arr(pat_plan* p, int slot, const float* a, size_t count, const float** dev, bool* host,
+                         cudaStream_t st) {
+  *host = false;
+  *dev = a;
+  if (!a || is_device_ptr(a)) return PAT_OK;
+  float* d;
+  PAT_TRY(stage(p, slot, count * sizeof(float), &d));
+  PAT_TRY_CUDA(cudaMemcpyAsync(d, a, count * sizeof(float), cudaMemcpyHostToDevice, st));
+  *dev = d;
+  *host = true;
+  return PAT_OK;
+}
+
+static pat_status out_arr(pat_plan* p, int slot, float* a, size_t count, float** dev, bool* host) {
+  *host = false;
+  *dev = a;
+  if (!a || is_device_ptr(a)) return PAT_OK;
+  PAT_TRY(stage(p, slot, count * sizeof(float), dev));
+  *host = true;
+  return PAT_OK;
+}
+
+static pat_status out_back(float* host_dst, const float* dev, size_t count, bool host, cudaStream_t st) {
+  if (!host) return PAT_OK;
+  PAT_TRY_CUDA(cudaMemcpyAsync(host_dst, dev, count * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PAT_TRY_CUDA(cudaStreamSynchronize(st));
+  return PAT_OK;
+}
+
+static pat_status check_plan(const pat_plan* p) {
+  if (!p) {
+    set_error("plan is NULL");
+    return PAT_ERR_INVALID;
+  }
+  return PAT_OK;
+}
+
+}  // namespace pat
+
+using namespace pat;
+
+extern "C" {
+
+pat_status pat_forward(pat_plan* plan, const float* x, float* y, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!x || (!y && plan->ns > 0)) {
+    set_error("x and y must not be NULL");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float* dx;
+  float* dy;
+  bool hx, hy;
+  PAT_TRY(in_arr(plan, 0, x, plan->N, &dx, &hx, st));
+  PAT_TRY(out_arr(plan, 1, y, ny, &dy, &hy));
+  if (plan->ns > 0) PAT_TRY(wave_forward(plan, dx, dy, st));
+  return out_back(y, dy, ny, hy, st);
+}
+
+pat_status pat_adjoint(pat_plan* plan, const float* y, float* x, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!x || (!y && plan->ns > 0)) {
+    set_error("x and y must not be NULL");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float* dy;
+  float* dx;
+  bool hx, hy;
+  PAT_TRY(in_arr(plan, 0, y, ny, &dy, &hy, st));
+  PAT_TRY(out_arr(plan, 1, x, plan->N, &dx, &hx));
+  if (plan->ns > 0) {
+    PAT_TRY(wave_adjoint(plan, dy, dx, st));
+  } else {
+    PAT_TRY_CUDA(fill_launch(dx, plan->N, 0.f, st));
+  }
+  return out_back(x, dx, plan->N, hx, st);
+}
+
+pat_status pat_Es(pat_plan* plan, double s, const float* u, float* x, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!u || !x || !std::isfinite(s)) {
+    set_error("u and x must not be NULL and s must be finite");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* du;
+  float* dx;
+  bool hu, hx;
+  PAT_TRY(in_arr(plan, 0, u, plan->N, &du, &hu, st));
+  PAT_TRY(out_arr(plan, 1, x, plan->N, &dx, &hx));
+  PAT_TRY(apply_Es(plan, s, du, dx, st));
+  return out_back(x, dx, plan->N, hx, st);
+}
+
+pat_status pat_EsT(pat_plan* plan, double s, const float* x, float* u, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!u || !x || !std::isfinite(s)) {
+    set_error("u and x must not be NULL and s must be finite");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* dx;
+  float* du;
+  bool hu, hx;
+  PAT_TRY(in_arr(plan, 0, x, plan->N, &dx, &hx, st));
+  PAT_TRY(out_arr(plan, 1, u, plan->N, &du, &hu));
+  PAT_TRY(apply_EsT(plan, s, dx, du, st));
+  return out_back(u, du, plan->N, hu, st);
+}
+
+pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int iters, const float* u0, float* u,
+                     float* x, double* log, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!y || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(s) || iters < 0) {
+    set_error("y must not be NULL, alpha finite and > 0, s finite, iters >= 0");
+    return PAT_ERR_INVALID;
+  }
+  if (log && !is_device_ptr(log)) {
+    set_error("log must be a device array");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float *dy, *du0;
+  float *du, *dx;
+  bool hy, hu0, hu, hx;
+  PAT_TRY(in_arr(plan, 0, y, ny, &dy, &hy, st));
+  PAT_TRY(in_arr(plan, 1, u0, plan->N, &du0, &hu0, st));
+  PAT_TRY(out_arr(plan, 2, u, plan->N, &du, &hu));
+  PAT_TRY(out_arr(plan, 3, x, plan->N, &dx, &hx));
+  PAT_TRY(solve_device(plan, dy, alpha, s, iters, du0, du, dx, log, st));
+  if (u) PAT_TRY(out_back(u, du, plan->N, hu, st));
+  if (x) PAT_TRY(out_back(x, dx, plan->N, hx, st));
+  return PAT_OK;
+}
+
+pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* ys, const double* alphas,
+                             const double* ss, int iters, float* const* xs, pat_status* per_inst, void* stream) {
+  if (B < 0 || (B > 0 && (!plans || !ys || !alphas || !ss || !xs))) {
+    set_error("batched solve: B >= 0 and all arrays are required");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  pat_status first = PAT_OK;
+  for (int i = 0; i < B; ++i) {
+    pat_status s = pat_solve(plans[i], ys[i], alphas[i], ss[i], iters, nullptr, nullptr, xs[i], nullptr, stream);
+    if (s == PAT_OK) s = pat_plan_check(plans[i], st);
+    if (per_inst) per_inst[i] = s;
+    if (s != PAT_OK && first == PAT_OK) first = s;
+  }
+  return first;
+}
+
+pat_status pat_plan_profile(pat_plan* plan, int enable) {
+  PAT_TRY(check_plan(plan));
+  plan->prof_on = enable != 0;
+  plan->prof_used = 0;
+  plan->prof_kernels = 0;
+  plan->prof_points = 0;
+  return PAT_OK;
+}
+
+pat_status pat_plan_profile_read(pat_plan* plan, long long* kernels, int* wave_calls, double* wave_ms,
+                                 long long* point_updates) {
+  PAT_TRY(check_plan(plan));
+  double total = 0.0;
+  for (int i = 0; i + 1 < plan->prof_used; i += 2) {
+    PAT_TRY_CUDA(cudaEventSynchronize(plan->prof_ev[i + 1]));
+    float ms = 0.f;
+    PAT_TRY_CUDA(cudaEventElapsedTime(&ms, plan->prof_ev[i], plan->prof_ev[i + 1]));
+    total += ms;
+  }
+  if (kernels) *kernels = plan->prof_kernels;
+  if (wave_calls) *wave_calls = plan->prof_used / 2;
+  if (wave_ms) *wave_ms = total;
+  if (point_updates) *point_updates = plan->prof_points;
+  return PAT_OK;
+}
+
+pat_status pat_plan_check(pat_plan* plan, void* stream) {
+  PAT_TRY(check_plan(plan));
+  cudaStream_t st = (cudaStream_t)stream;
+  PAT_TRY_CUDA(cudaStreamSynchronize(st));
+  int status = 0;
+  PAT_TRY_CUDA(cudaMemcpy(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int zero = 0;
+  PAT_TRY_CUDA(cudaMemcpy(plan->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (status == PAT_ERR_TIMEOUT) set_error("a bounded wait in the persistent wave kernel ran out");
+  if (status == PAT_ERR_BREAKDOWN) set_error("CG breakdown: p.q <= 0 or a non-finite step length");
+  return (pat_status)status;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Definition of the opaque plan object behind the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+
+struct pat_plan {
+  // ---- problem
+  int dim = 2;
+  int n[3] = {1, 1, 1};  // nx, ny, nz
+  long long N = 0;
+  double h = 0, dt = 0;
+  int nt = 0, order = 2, M = 1, R = 1, ns = 0, corners = 4;
+  double c_max = 0;
+  bool varc = false;
+  float kappa0 = 0.f;
+  float* d_kappa = nullptr;
+  float w[pat::kMaxR + 1] = {0};  // composed stencil weights w[1..R]
+
+  // ---- sensors: sampling (ns x corners) and the transposed injection CSR
+  int* d_sens_cell = nullptr;
+  float* d_sens_w = nullptr;
+  std::vector<int> h_sens_cell;
+  std::vector<float> h_sens_w;
+  int n_inj = 0;
+  int* d_inj_cell = nullptr;
+  int* d_inj_ptr = nullptr;
+  int* d_ent_sensor = nullptr;
+  float* d_ent_w = nullptr;
+  std::vector<int> h_inj_cell, h_inj_ptr;
+
+  // ---- wavelet
+  int family = 1, L = 2, levels = 1, level_offset = 0;
+  float hf[pat::kMaxTaps] = {0}, gf[pat::kMaxTaps] = {0};
+
+  // ---- wave engine
+  int path = PAT_PATH_STEP;       // engine in use
+  bool persist_ok = false;        // persistent engine available for this plan
+  int tiles_x = 0, tiles_y = 0, ntiles = 0;
+  int* d_tile_samp_ptr = nullptr;
+  pat::SampEntry* d_samp = nullptr;
+  int* d_tile_inj_ptr = nullptr;
+  pat::InjCell* d_tinj = nullptr;
+  float* d_xbuf = nullptr;
+  int* d_flags = nullptr;
+  unsigned* d_epoch = nullptr;
+  unsigned* d_done = nullptr;
+  int* d_abort = nullptr;
+  long long timeout_ns = 2000000000LL;
+  float* d_wv[3] = {nullptr, nullptr, nullptr};  // per-step engine fields
+
+  // ---- wavelet scratch
+  float* d_dwt_a = nullptr;  // approximation ping-pong (2 x N/2^dim)
+  float* d_dwt_b = nullptr;
+  float* d_dwt_t1 = nullptr;  // 3D separable-pass intermediates (N each)
+  float* d_dwt_t2 = nullptr;
+
+  // ---- solver workspace
+  float *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_img = nullptr, *d_u = nullptr, *d_ybuf = nullptr;
+  pat::CgScalars* d_sc = nullptr;
+  double* d_partials = nullptr;
+  unsigned* d_counter = nullptr;
+  int* d_status = nullptr;
+
+  // ---- staging for host arrays
+  float* d_stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t stage_bytes[4] = {0, 0, 0, 0};
+
+  // ---- measurement hooks
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
+  int prof_used = 0;                 // events used (2 per wave application)
+  long long prof_kernels = 0;
+  long long prof_points = 0;
+
+  std::vector<void*> allocations;
+};
+
+namespace pat {
+pat_status plan_alloc(pat_plan* p, void** ptr, size_t bytes, const char* what);
+pat_status wave_forward(pat_plan* p, const float* x, float* y, cudaStream_t st);
+pat_status wave_adjoint(pat_plan* p, const float* y, float* x, cudaStream_t st);
+pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_t st);
+pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream_t st);
+pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int iters, const float* u0, float* u,
+                        float* x, double* log, cudaStream_t st);
+}  // namespace pat

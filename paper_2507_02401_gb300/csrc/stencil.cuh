@@ -1,0 +1,101 @@
+// Device helpers shared by the wave kernels.
+//
+// The composed Laplacian L = -G^T G of the staggered scheme (paper Sec. 2,
+// Eq. wave_equation; order 2M, radius R = 2M-1) is evaluated along each axis
+// in the zero-sum form
+//
+//     (L P)_i = sum_{m=1..R} w_m ((P_{i+m} + P_{i-m}) - 2 P_i),
+//
+// so that L annihilates constants exactly in FP32 whatever the rounding of
+// w_m.  (The usual form w_0 P_i + sum w_m (P_{i+m} + P_{i-m}) with a rounded
+// w_0 adds a spurious mass term that shifts the low-frequency modes and, over
+// a few thousand leapfrog steps, costs ~1e-5 relative accuracy.)
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pat {
+
+__device__ __forceinline__ float f4get(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+// Laplacian of a 2 (rows) x 4 (cols) block from a shared-memory tile.
+//   S      tile base, row pitch `pitch` floats (pitch % 4 == 0)
+//   srow   tile row of the block's first row (>= R, with R rows of halo
+//          above and R + 1 below available)
+//   scol   tile column of the block's first column (multiple of 4, >= 8,
+//          with 8 columns of halo on the left and right available)
+template <int R>
+__device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, int srow, int scol,
+                                        const float* __restrict__ w, float L[2][4]) {
+  // y direction: the block's four columns over rows srow-R .. srow+1+R
+  float4 col[2 + 2 * R];
+#pragma unroll
+  for (int i = 0; i < 2 + 2 * R; ++i) col[i] = *reinterpret_cast<const float4*>(S + (srow - R + i) * pitch + scol);
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float c = f4get(col[rr + R], j);
+      const float c2 = c + c;
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], (f4get(col[rr + R + m], j) + f4get(col[rr + R - m], j)) - c2, acc);
+      L[rr][j] = acc;
+    }
+  }
+  // x direction: each row over columns scol-8 .. scol+11
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    float f[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(S + (srow + rr) * pitch + scol - 8 + 4 * q);
+      f[4 * q + 0] = v.x;
+      f[4 * q + 1] = v.y;
+      f[4 * q + 2] = v.z;
+      f[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float c = f[8 + j];
+      const float c2 = c + c;
+      float acc = L[rr][j];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], (f[8 + j + m] + f[8 + j - m]) - c2, acc);
+      L[rr][j] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- memory ops
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace pat

@@ -1,0 +1,112 @@
+"""Plan: owning Python handle of a pat_plan (argument marshalling only)."""
+import numpy as np
+import torch
+
+from . import _lib
+
+
+class Plan:
+    """One reconstruction problem on the GPU.
+
+    shape    grid shape in array order, (ny, nx) or (nz, ny, nx), x fastest
+    h, dt    spacing [m] and time step [s];  nt samples (P^0 .. P^{nt-1})
+    order    staggered order 2/4/6/8;  c: scalar [m/s] or array of `shape`
+    sensors  (Ns, d) coordinates (x, y[, z]) [m]
+    family, levels, level_offset: periodic Daubechies wavelet of E_s
+    """
+
+    def __init__(self, shape, h, dt, nt, order, c, sensors, family=4, levels=3, level_offset=0, stream=None):
+        self.shape = tuple(int(s) for s in shape)
+        self.dim = len(self.shape)
+        grid = _lib.pat_grid()
+        grid.dim = self.dim
+        n = list(self.shape[::-1]) + [1] * (3 - self.dim)
+        for i in range(3):
+            grid.n[i] = n[i]
+        grid.h = float(h)
+        wav = _lib.pat_wavelet()
+        wav.family, wav.levels, wav.level_offset = int(family), int(levels), int(level_offset)
+        c_arr = None
+        c0 = 0.0
+        if np.ndim(c) == 0:
+            c0 = float(c)
+        else:
+            c_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), self.shape))
+        sens = np.ascontiguousarray(np.asarray(sensors, dtype=np.float64).reshape(-1, self.dim))
+        self.ns = sens.shape[0]
+        self.nt = int(nt)
+        self.N = int(np.prod(self.shape))
+        self.handle = _lib.pat_plan_create(grid, c_arr, c0, sens, self.ns, float(dt), self.nt, int(order), wav, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pat_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- helpers
+    def _stream(self, stream):
+        if stream is not None:
+            return stream
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream()
+        return None
+
+    @staticmethod
+    def _f32(t, device="cuda"):
+        if isinstance(t, torch.Tensor):
+            return t.to(device=device, dtype=torch.float32).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(t, dtype=np.float32), device=device)
+
+    @property
+    def path(self):
+        return _lib.pat_plan_get_path(self.handle)
+
+    @path.setter
+    def path(self, p):
+        _lib.pat_plan_set_path(self.handle, p)
+
+    def check(self, stream=None):
+        return _lib.pat_plan_check(self.handle, self._stream(stream))
+
+    # -------------------------------------------------------------- operators
+    def forward(self, x, out=None, stream=None):
+        """y = K x on the device; returns a (Ns, nt) float32 tensor."""
+        x = self._f32(x)
+        y = out if out is not None else torch.empty((self.ns, self.nt), device="cuda", dtype=torch.float32)
+        _lib.pat_forward(self.handle, x, y, self._stream(stream))
+        return y
+
+    def adjoint(self, y, out=None, stream=None):
+        """x = K* y; returns a float32 tensor of `shape`."""
+        y = self._f32(y)
+        x = out if out is not None else torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        _lib.pat_adjoint(self.handle, y, x, self._stream(stream))
+        return x
+
+    def Es(self, u, s, out=None, stream=None):
+        u = self._f32(u)
+        x = out if out is not None else torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        _lib.pat_Es(self.handle, s, u, x, self._stream(stream))
+        return x
+
+    def EsT(self, x, s, out=None, stream=None):
+        x = self._f32(x)
+        u = out if out is not None else torch.empty(self.N, device="cuda", dtype=torch.float32)
+        _lib.pat_EsT(self.handle, s, x, u, self._stream(stream))
+        return u
+
+    def solve(self, y, alpha, s, iters, u0=None, want_log=False, stream=None):
+        """CG solve; returns (u, x, log) as device tensors (log: (iters, 3) float64 or None)."""
+        y = self._f32(y)
+        u = torch.empty(self.N, device="cuda", dtype=torch.float32)
+        x = torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        log = torch.zeros((max(iters, 1), 3), device="cuda", dtype=torch.float64) if want_log else None
+        u0t = self._f32(u0) if u0 is not None else None
+        _lib.pat_solve(self.handle, y, alpha, s, iters, u0t, u, x, log, self._stream(stream))
+        return u, x, (log[:iters] if want_log else None)
