@@ -128,8 +128,8 @@ class Wavelet:
         self.dim = len(self.shape)
         if family not in FAMILIES:
             raise ValueError("family must be 1 (haar), 2 (db2) or 4 (db4)")
-        if levels < 1 or any(s % (1 << levels) for s in self.shape):
-            raise ValueError("every extent must be divisible by 2**levels")
+        if levels < 0 or any(s % (1 << levels) for s in self.shape):
+            raise ValueError("levels must be >= 0 and every extent divisible by 2**levels")
         self.levels = int(levels)
         self.level_offset = int(level_offset)
         self.h = daubechies(family)

@@ -33,10 +33,15 @@ pat_status cuda_fail(cudaError_t e, const char* what);
 
 // ------------------------------------------------------- device structs
 // One sensor's bilinear sampling entry inside a persistent 2D tile.
+// A sensor whose 2x2 interpolation block straddles four tiles (its base cell
+// is a tile's last row and column) cannot be read from one tile's cross-shaped
+// halo; each of its four cells is then sampled by the tile that owns it into
+// part[(4*q + corner)*nt + t] and a small kernel sums the four afterwards.
 struct SampEntry {
   int sensor;
-  short lx, ly;  // base cell in tile-local coordinates
-  float w[4];    // weights of (lx,ly), (lx+1,ly), (lx,ly+1), (lx+1,ly+1)
+  int part;      // -1: whole sensor sampled here; else 4*q + corner of a split sensor
+  short lx, ly;  // base cell (or the split corner's cell) in tile-local coordinates
+  float w[4];    // weights of (lx,ly), (lx+1,ly), (lx,ly+1), (lx+1,ly+1); split: w[0] only
 };
 
 // One injected cell inside a persistent 2D tile: entries [beg, end) of the
@@ -52,36 +57,52 @@ struct Persist2DArgs {
   int tiles_x, tiles_y;
   float w[kMaxR + 1];  // composed stencil weights, w[1..R]
   float kappa0;        // (c dt / h)^2 when the medium is constant
+  float kappa0_lo;     // kappa0 - fl(kappa0) (rounding residual)
   const float* kappa;  // per-cell kappa, or nullptr
+  const float* kappa_lo;  // per-cell rounding residual of kappa, or nullptr
   const float* in;     // forward: x (N);  adjoint: y (ns*nt)
   float* out;          // forward: y;      adjoint: x
   const int* tile_samp_ptr;
   const SampEntry* samp;
+  float* part;  // split-sensor partial samples (4 x nt per split sensor)
   const int* tile_inj_ptr;
   const InjCell* inj;
   const int* ent_sensor;
   const float* ent_w;
-  float* xbuf;           // boundary strips, 2 slots per tile
-  int* flags;            // per-tile published state counter
+  void* xbuf;            // tagged boundary strips (64-bit words), 2 slots per tile
   unsigned* epoch;       // launch counter (device)
   unsigned* done;        // CTAs finished in this launch
   int* abort;            // set when any CTA gives up
   int* status;           // sticky plan status
   long long timeout_ns;  // bound on any single wait
+  int poll_ns;           // back-off between polls of the exchange (0 = spin)
 };
 
-// Arguments of the per-step kernels (2D tile kernel and 3D z-marching kernel).
+// Arguments of the per-step kernels.
+//   2D (increment form): d = (d_zero ? 0 : dbuf) + c_lap kappa L cur, dbuf = d,
+//      next = cur + d; with final = 1 (adjoint's last step) next = dbuf + c_lap L(kappa cur).
+//   3D (three-level form): next = c_cur cur - c_prev prev + c_lap kappa L cur
+//      (adjoint: L(kappa cur)).
+//   2D adjoint carries compensation terms: cur_lo/next_lo for Q, dbuf_lo for G,
+//      and feeds the stencil kappa*Q as a hi + lo pair.
 struct StepArgs {
   int nx, ny, nz;
   float w[kMaxR + 1];
-  float kappa0;
-  const float* kappa;  // or nullptr
+  float kappa0, kappa0_lo;
+  const float* kappa;     // or nullptr
+  const float* kappa_lo;  // rounding residual of kappa, or nullptr
   const float* cur;    // P^n (forward) or Q^{n+1} (adjoint)
-  const float* prev;   // P^{n-1} or Q^{n+2}   (nullptr on the first step)
-  float* next;         // P^{n+1} or Q^n
+  const float* cur_lo;  // 2D adjoint: compensation of Q^{n+1}
+  float* next_lo;       // 2D adjoint: compensation of Q^n
+  float* dbuf_lo;       // 2D adjoint: compensation of G
+  const float* prev;   // 3D: P^{n-1} or Q^{n+2}   (nullptr = 0)
+  float* dbuf;         // 2D: increment D (forward) / G (adjoint), updated in place
+  int d_zero;          // 2D: treat the incoming increment as 0
+  int final_step;      // 2D adjoint: next = dbuf + c_lap L(kappa cur)
+  float* next;         // P^{n+1} or Q^n (or the adjoint's result)
   float c_lap;         // coefficient of kappa*L (1, or 0.5 for the first/last step)
-  float c_cur;         // coefficient of the current field (2, or 1)
-  float c_prev;        // coefficient of the previous field (1, or 0)
+  float c_cur;         // 3D: coefficient of the current field (2, or 1)
+  float c_prev;        // 3D: coefficient of the previous field (1, or 0)
   // fused sampling of `cur` (forward): y[s*nt + t_sample] for s in [0, ns)
   int ns, nt, t_sample;
   const int* sens_cell;
@@ -96,8 +117,11 @@ bool persist2d_supported(int R, bool varc);
 int persist2d_tile_x();
 int persist2d_tile_y();
 size_t persist2d_smem_bytes(int R, bool adj);
+size_t persist2d_xbuf_words(int R, bool adj, int ntiles);  // 64-bit exchange words
 int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
+cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, int nsplit, int nt, float* y,
+                                    cudaStream_t st);
 
 // wave_step.cu
 cudaError_t step2d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);

@@ -16,20 +16,23 @@ static Persist2DArgs persist_args(pat_plan* p) {
   a.tiles_y = p->tiles_y;
   for (int m = 0; m <= kMaxR; ++m) a.w[m] = p->w[m];
   a.kappa0 = p->kappa0;
+  a.kappa0_lo = p->kappa0_lo;
   a.kappa = p->varc ? p->d_kappa : nullptr;
+  a.kappa_lo = p->varc ? p->d_kappa_lo : nullptr;
   a.tile_samp_ptr = p->d_tile_samp_ptr;
   a.samp = p->d_samp;
+  a.part = p->d_part;
   a.tile_inj_ptr = p->d_tile_inj_ptr;
   a.inj = p->d_tinj;
   a.ent_sensor = p->d_ent_sensor;
   a.ent_w = p->d_ent_w;
   a.xbuf = p->d_xbuf;
-  a.flags = p->d_flags;
   a.epoch = p->d_epoch;
   a.done = p->d_done;
   a.abort = p->d_abort;
   a.status = p->d_status;
   a.timeout_ns = p->timeout_ns;
+  a.poll_ns = p->poll_ns;
   return a;
 }
 
@@ -40,7 +43,9 @@ static StepArgs step_args(pat_plan* p) {
   a.nz = p->n[2];
   for (int m = 0; m <= kMaxR; ++m) a.w[m] = p->w[m];
   a.kappa0 = p->kappa0;
+  a.kappa0_lo = p->kappa0_lo;
   a.kappa = p->varc ? p->d_kappa : nullptr;
+  a.kappa_lo = p->varc ? p->d_kappa_lo : nullptr;
   a.ns = p->ns;
   a.nt = p->nt;
   a.sens_cell = p->d_sens_cell;
@@ -75,6 +80,7 @@ static pat_status wave_forward_impl(pat_plan* p, const float* x, float* y, cudaS
     a.in = x;
     a.out = y;
     PAT_TRY_CUDA(persist2d_launch(p->R, false, p->varc, a, p->ntiles, st));
+    PAT_TRY_CUDA(persist2d_split_combine(p->d_part, p->d_split_sensor, p->nsplit, p->nt, y, st));
     return PAT_OK;
   }
   const int nt = p->nt;
@@ -82,9 +88,24 @@ static pat_status wave_forward_impl(pat_plan* p, const float* x, float* y, cudaS
     PAT_TRY_CUDA(sample_launch(x, p->ns, nt, 0, p->d_sens_cell, p->d_sens_w, p->corners, y, st));
     return PAT_OK;
   }
-  // F_0 = x, F_n = wv[(n-1) % 3] for n >= 1; step n makes F_{n+1} and samples F_n
   StepArgs a = step_args(p);
   a.y = y;
+  if (p->dim == 2) {
+    // increment form: F_0 = x, F_n = wv[(n-1) % 2], D = wv[2]; step n makes F_{n+1}, samples F_n
+    a.dbuf = p->d_wv[2];
+    for (int n = 0; n < nt - 1; ++n) {
+      a.cur = (n == 0) ? x : p->d_wv[(n - 1) % 2];
+      a.next = p->d_wv[n % 2];
+      a.d_zero = (n == 0);
+      a.c_lap = (n == 0) ? 0.5f : 1.f;
+      a.t_sample = n;
+      PAT_TRY_CUDA(step_launch(p, false, a, st));
+    }
+    PAT_TRY_CUDA(sample_launch(p->d_wv[(nt - 2) % 2], p->ns, nt, nt - 1, p->d_sens_cell, p->d_sens_w, p->corners,
+                               y, st));
+    return PAT_OK;
+  }
+  // three-level form: F_0 = x, F_n = wv[(n-1) % 3]
   for (int n = 0; n < nt - 1; ++n) {
     a.cur = (n == 0) ? x : p->d_wv[(n - 1) % 3];
     a.prev = (n == 0) ? nullptr : (n == 1 ? x : p->d_wv[(n - 2) % 3]);
@@ -116,12 +137,45 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
     PAT_TRY_CUDA(inject(x, 0));
     return PAT_OK;
   }
-  // Q^m lives in wv[(nt-1-m) % 3]
+  StepArgs a = step_args(p);
+  a.y = nullptr;
+  if (p->dim == 2) {
+    // increment form with compensation: G = wv[2] (+ wv[5]); Q^m in wv[(nt-m) % 2]
+    // (+ wv[3 + (nt-m) % 2]) with Q^nt = 0
+    float* G = p->d_wv[2];
+    auto Qbuf = [&](int m) { return p->d_wv[(nt - m) % 2]; };
+    auto Qlo = [&](int m) { return p->d_wv[3 + (nt - m) % 2]; };
+    PAT_TRY_CUDA(fill_launch(G, p->N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(p->d_wv[5], p->N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(Qbuf(nt), p->N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(Qlo(nt), p->N, 0.f, st));
+    a.dbuf = G;
+    a.dbuf_lo = p->d_wv[5];
+    for (int m = nt - 1; m >= 1; --m) {
+      PAT_TRY_CUDA(inject(G, m));  // G^{m+1} + S^T r_m
+      a.cur = Qbuf(m + 1);
+      a.cur_lo = Qlo(m + 1);
+      a.next = Qbuf(m);
+      a.next_lo = Qlo(m);
+      a.d_zero = 0;
+      a.final_step = 0;
+      a.c_lap = 1.f;
+      PAT_TRY_CUDA(step_launch(p, true, a, st));
+    }
+    PAT_TRY_CUDA(inject(G, 0));
+    a.cur = Qbuf(1);
+    a.cur_lo = Qlo(1);
+    a.next = x;
+    a.next_lo = nullptr;
+    a.final_step = 1;
+    a.c_lap = 0.5f;
+    PAT_TRY_CUDA(step_launch(p, true, a, st));
+    return PAT_OK;
+  }
+  // three-level form: Q^m lives in wv[(nt-1-m) % 3]
   auto Qbuf = [&](int m) { return p->d_wv[(nt - 1 - m) % 3]; };
   PAT_TRY_CUDA(fill_launch(Qbuf(nt - 1), p->N, 0.f, st));
   PAT_TRY_CUDA(inject(Qbuf(nt - 1), nt - 1));
-  StepArgs a = step_args(p);
-  a.y = nullptr;
   for (int m = nt - 2; m >= 1; --m) {
     a.cur = Qbuf(m + 1);
     a.prev = (m + 2 <= nt - 1) ? Qbuf(m + 2) : nullptr;
@@ -155,11 +209,13 @@ static pat_status prof_mark(pat_plan* p, cudaStream_t st) {
 }
 
 static long long wave_kernels(const pat_plan* p, bool adj) {
-  if (p->path == PAT_PATH_PERSISTENT) return 1;
+  if (p->path == PAT_PATH_PERSISTENT) return (!adj && p->nsplit > 0) ? 2 : 1;
   const long long nt = p->nt;
   if (nt == 1) return adj ? 2 : 1;
-  if (!adj) return nt;         // nt-1 steps + final sample
-  return 2 + 2 * (nt - 2) + 2;  // fill+inject, (step+inject) x (nt-2), final step+inject
+  if (!adj) return nt;  // nt-1 steps + final sample
+  const long long inj = p->n_inj > 0 ? 1 : 0;
+  if (p->dim == 2) return 4 + (nt - 1) * (1 + inj) + (1 + inj);  // 4 fills, (inject+step) x (nt-1), final
+  return (1 + inj) + (nt - 2) * (1 + inj) + (1 + inj);             // fill+inject, (step+inject), final
 }
 
 pat_status wave_forward(pat_plan* p, const float* x, float* y, cudaStream_t st) {
@@ -204,6 +260,10 @@ static long long band_offset(const pat_plan* p, int i, int b) {
 
 pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream_t st) {
   const int m = p->levels;
+  if (m == 0) {  // no levels: W = I, the coefficients are the image
+    if (u != x) PAT_TRY_CUDA(cudaMemcpyAsync(u, x, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, st));
+    return PAT_OK;
+  }
   float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
   const float* in = x;
   for (int i = 1; i <= m; ++i) {
@@ -236,6 +296,10 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
 
 pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_t st) {
   const int m = p->levels;
+  if (m == 0) {
+    if (u != x) PAT_TRY_CUDA(cudaMemcpyAsync(x, u, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, st));
+    return PAT_OK;
+  }
   float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
   const float* approx = u;
   for (int i = m; i >= 1; --i) {

@@ -168,19 +168,43 @@ static pat_status setup_persistent(pat_plan* p, cudaStream_t st) {
   p->ntiles = p->tiles_x * p->tiles_y;
   const int nx = p->n[0];
 
-  // sampling entries grouped by the tile holding each sensor's base cell
+  // sampling entries grouped by the tile holding each sensor's base cell; a
+  // sensor whose 2x2 block crosses a tile corner is split into four parts
   std::vector<std::vector<SampEntry>> per_tile(p->ntiles);
+  std::vector<int> split_sensor;
   for (int s = 0; s < p->ns; ++s) {
     const int c0 = p->h_sens_cell[s * 4];
     const int bx = c0 % nx, by = c0 / nx;
-    const int tile = (by / TY) * p->tiles_x + bx / TX;
-    SampEntry e;
-    e.sensor = s;
-    e.lx = (short)(bx % TX);
-    e.ly = (short)(by % TY);
-    for (int k = 0; k < 4; ++k) e.w[k] = p->h_sens_w[s * 4 + k];
-    per_tile[tile].push_back(e);
+    const bool split = (bx % TX == TX - 1) && (by % TY == TY - 1);
+    if (!split) {
+      const int tile = (by / TY) * p->tiles_x + bx / TX;
+      SampEntry e;
+      e.sensor = s;
+      e.part = -1;
+      e.lx = (short)(bx % TX);
+      e.ly = (short)(by % TY);
+      for (int k = 0; k < 4; ++k) e.w[k] = p->h_sens_w[s * 4 + k];
+      per_tile[tile].push_back(e);
+      continue;
+    }
+    const int q = (int)split_sensor.size();
+    split_sensor.push_back(s);
+    for (int k = 0; k < 4; ++k) {
+      const int cell = p->h_sens_cell[s * 4 + k];
+      const int cx = cell % nx, cy = cell / nx;
+      SampEntry e;
+      e.sensor = s;
+      e.part = 4 * q + k;
+      e.lx = (short)(cx % TX);
+      e.ly = (short)(cy % TY);
+      e.w[0] = p->h_sens_w[s * 4 + k];
+      e.w[1] = e.w[2] = e.w[3] = 0.f;
+      per_tile[(cy / TY) * p->tiles_x + cx / TX].push_back(e);
+    }
   }
+  p->nsplit = (int)split_sensor.size();
+  PAT_TRY(upload(p, &p->d_split_sensor, split_sensor, "split sensors", st));
+  PAT_TRY(alloc_n(p, &p->d_part, (size_t)4 * p->nsplit * p->nt, "split sensor parts"));
   std::vector<int> samp_ptr(p->ntiles + 1, 0);
   std::vector<SampEntry> samp;
   for (int t = 0; t < p->ntiles; ++t) {
@@ -213,18 +237,19 @@ static pat_status setup_persistent(pat_plan* p, cudaStream_t st) {
   PAT_TRY(upload(p, &p->d_samp, samp, "tile sampling entries", st));
   PAT_TRY(upload(p, &p->d_tile_inj_ptr, inj_ptr, "tile injection offsets", st));
   PAT_TRY(upload(p, &p->d_tinj, inj, "tile injection cells", st));
-  const size_t strip = (size_t)2 * p->R * (TX + TY);
-  PAT_TRY(alloc_n(p, &p->d_xbuf, (size_t)p->ntiles * 2 * strip, "exchange strips"));
-  PAT_TRY(alloc_n(p, &p->d_flags, (size_t)p->ntiles, "tile flags"));
+  // tagged exchange words (the adjoint exchanges two fields); tags start at
+  // epoch 1 << 20, so the zeroed buffer never matches
+  const size_t words = persist2d_xbuf_words(p->R, true, p->ntiles);
+  PAT_TRY(plan_alloc(p, &p->d_xbuf, words * 8, "exchange strips"));
+  if (const char* e = getenv("PAT_POLL_NS")) p->poll_ns = std::max(0, atoi(e));
   PAT_TRY(alloc_n(p, &p->d_epoch, 1, "epoch"));
   PAT_TRY(alloc_n(p, &p->d_done, 1, "done counter"));
   PAT_TRY(alloc_n(p, &p->d_abort, 1, "abort flag"));
-  PAT_TRY_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(int) * p->ntiles, st));
   const unsigned one = 1u;
   PAT_TRY_CUDA(cudaMemcpyAsync(p->d_epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaMemsetAsync(p->d_done, 0, sizeof(unsigned), st));
   PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
-  PAT_TRY_CUDA(cudaMemsetAsync(p->d_xbuf, 0, sizeof(float) * p->ntiles * 2 * strip, st));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->d_xbuf, 0, words * 8, st));
   return PAT_OK;
 }
 
@@ -270,8 +295,8 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
     set_error("wavelet family must be 1 (haar), 2 (db2) or 4 (db4)");
     return PAT_ERR_INVALID;
   }
-  if (wav->levels < 1 || wav->levels > kMaxLevels || wav->level_offset < 0) {
-    set_error("wavelet levels must be in [1, %d] and level_offset >= 0", kMaxLevels);
+  if (wav->levels < 0 || wav->levels > kMaxLevels || wav->level_offset < 0) {
+    set_error("wavelet levels must be in [0, %d] and level_offset >= 0", kMaxLevels);
     return PAT_ERR_INVALID;
   }
   for (int a = 0; a < p->dim; ++a)
@@ -325,14 +350,20 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   composed_weights(p->M, wd);
   for (int m = 0; m <= p->R; ++m) p->w[m] = (float)wd[m];
   p->varc = !constant;
-  p->kappa0 = (float)((c0 * dt / p->h) * (c0 * dt / p->h));
+  {
+    const double k0 = (c0 * dt / p->h) * (c0 * dt / p->h);
+    p->kappa0 = (float)k0;
+    p->kappa0_lo = (float)(k0 - (double)p->kappa0);
+  }
   if (p->varc) {
-    std::vector<float> kap(p->N);
+    std::vector<float> kap(p->N), kap_lo(p->N);
     for (long long i = 0; i < p->N; ++i) {
       const double r = c[i] * dt / p->h;
       kap[i] = (float)(r * r);
+      kap_lo[i] = (float)(r * r - (double)kap[i]);
     }
     PAT_TRY(upload(p, &p->d_kappa, kap, "kappa", st));
+    PAT_TRY(upload(p, &p->d_kappa_lo, kap_lo, "kappa residual", st));
   }
 
   // ---- sensors: interpolation weights in FP64, cell index floor(u) clamped to n-2
@@ -408,7 +439,7 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
 
   // ---- workspace
   const size_t N = (size_t)p->N;
-  for (int i = 0; i < 3; ++i) PAT_TRY(alloc_n(p, &p->d_wv[i], N, "wave fields"));
+  for (int i = 0; i < (p->dim == 2 ? 6 : 3); ++i) PAT_TRY(alloc_n(p, &p->d_wv[i], N, "wave fields"));
   PAT_TRY(alloc_n(p, &p->d_dwt_a, N >> p->dim, "dwt approximation"));
   PAT_TRY(alloc_n(p, &p->d_dwt_b, N >> p->dim, "dwt approximation"));
   if (p->dim == 3) {

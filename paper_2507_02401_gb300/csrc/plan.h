@@ -15,7 +15,9 @@ struct pat_plan {
   double c_max = 0;
   bool varc = false;
   float kappa0 = 0.f;
+  float kappa0_lo = 0.f;  // rounding residual of kappa0
   float* d_kappa = nullptr;
+  float* d_kappa_lo = nullptr;  // rounding residual of kappa (varying medium)
   float w[pat::kMaxR + 1] = {0};  // composed stencil weights w[1..R]
 
   // ---- sensors: sampling (ns x corners) and the transposed injection CSR
@@ -40,15 +42,18 @@ struct pat_plan {
   int tiles_x = 0, tiles_y = 0, ntiles = 0;
   int* d_tile_samp_ptr = nullptr;
   pat::SampEntry* d_samp = nullptr;
+  int nsplit = 0;                 // sensors sampled as four per-tile parts
+  int* d_split_sensor = nullptr;
+  float* d_part = nullptr;
   int* d_tile_inj_ptr = nullptr;
   pat::InjCell* d_tinj = nullptr;
-  float* d_xbuf = nullptr;
-  int* d_flags = nullptr;
+  void* d_xbuf = nullptr;  // tagged 64-bit exchange words
   unsigned* d_epoch = nullptr;
   unsigned* d_done = nullptr;
   int* d_abort = nullptr;
   long long timeout_ns = 2000000000LL;
-  float* d_wv[3] = {nullptr, nullptr, nullptr};  // per-step engine fields
+  int poll_ns = 0;  // exchange polling back-off
+  float* d_wv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per-step engine fields
 
   // ---- wavelet scratch
   float* d_dwt_a = nullptr;  // approximation ping-pong (2 x N/2^dim)

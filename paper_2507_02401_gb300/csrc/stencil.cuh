@@ -20,13 +20,23 @@ __device__ __forceinline__ float f4get(const float4& v, int j) {
   return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
-// Laplacian of a 2 (rows) x 4 (cols) block from a shared-memory tile.
+// Pair term of one stencil offset: (a + b) - 2c, or in the difference form
+// (a - c) + (b - c), whose differences are exact (Sterbenz) wherever the
+// field is smooth, so the rounding error follows the local variation rather
+// than the field's magnitude.
+template <bool DIFF>
+__device__ __forceinline__ float pair_term(float a, float b, float c, float c2) {
+  return DIFF ? (a - c) + (b - c) : (a + b) - c2;
+}
+
+// Laplacian of a 2 (rows) x 4 (cols) block from a shared-memory tile,
+// accumulated into L (ACC) or written to it.
 //   S      tile base, row pitch `pitch` floats (pitch % 4 == 0)
 //   srow   tile row of the block's first row (>= R, with R rows of halo
 //          above and R + 1 below available)
 //   scol   tile column of the block's first column (multiple of 4, >= 8,
 //          with 8 columns of halo on the left and right available)
-template <int R>
+template <int R, bool DIFF = false, bool ACC = false>
 __device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, int srow, int scol,
                                         const float* __restrict__ w, float L[2][4]) {
   // y direction: the block's four columns over rows srow-R .. srow+1+R
@@ -39,9 +49,10 @@ __device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, 
     for (int j = 0; j < 4; ++j) {
       const float c = f4get(col[rr + R], j);
       const float c2 = c + c;
-      float acc = 0.f;
+      float acc = ACC ? L[rr][j] : 0.f;
 #pragma unroll
-      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], (f4get(col[rr + R + m], j) + f4get(col[rr + R - m], j)) - c2, acc);
+      for (int m = 1; m <= R; ++m)
+        acc = fmaf(w[m], pair_term<DIFF>(f4get(col[rr + R + m], j), f4get(col[rr + R - m], j), c, c2), acc);
       L[rr][j] = acc;
     }
   }
@@ -63,10 +74,19 @@ __device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, 
       const float c2 = c + c;
       float acc = L[rr][j];
 #pragma unroll
-      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], (f[8 + j + m] + f[8 + j - m]) - c2, acc);
+      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], pair_term<DIFF>(f[8 + j + m], f[8 + j - m], c, c2), acc);
       L[rr][j] = acc;
     }
   }
+}
+
+// Knuth's TwoSum: returns s = fl(a + b) and sets e so that s + e == a + b
+// exactly (no reassociation: the library is built without fast-math).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+  return s;
 }
 
 // ---------------------------------------------------------------- memory ops

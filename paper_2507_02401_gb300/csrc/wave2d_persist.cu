@@ -14,45 +14,147 @@
 // which is the exact transpose of the forward program.  The increment form
 // keeps FP32 rounding from being amplified in the low-frequency modes.
 //
-// GB300 mapping: the grid is cut into 64 x 32 tiles, one CTA per tile, all
+// Precision.  kappa is applied as an unevaluated pair kappa_hi + kappa_lo:
+// with a constant medium a rounded kappa is the same everywhere and shifts
+// the phase of every mode coherently, step after step.  In the adjoint the
+// state Q integrates G over time and, in a closed (reflecting) box, grows an
+// order of magnitude beyond the result, so G and Q are kept as compensated
+// pairs (TwoSum) and the stencil receives kappa*Q as a hi + lo pair of FP32
+// fields (hi through the difference-form stencil, lo through the cheap form).
+//
+// GB300 mapping.  The grid is cut into 64 x 32 tiles, one CTA per tile, all
 // co-resident (cooperative launch).  Each thread keeps its 2 x 4 cells' state
-// (P, D, kappa) in registers for the whole loop; the CTA keeps the current
-// field plus an R-deep halo in shared memory (double buffered).  After each
-// step a CTA publishes only its R-deep boundary strips to an L2-resident
-// exchange buffer and bumps a per-tile flag (release); the four neighbours
-// wait on that flag (acquire) and copy the strips into their halo.  No
-// grid-wide barrier and no per-step launch.  Every wait is bounded by a
-// global-timer limit and by a shared abort flag; a CTA that gives up records
+// in registers for the whole loop; the CTA keeps the current field plus an
+// R-deep halo in shared memory (double buffered).  After each step a CTA
+// writes its R-deep boundary strips to an L2-resident exchange buffer, every
+// value packed with the step it belongs to into one 64-bit word; an aligned
+// 64-bit access is single-copy atomic, so a neighbour that reads a word with
+// the expected tag has the right value: no flags, no fences, one L2 round
+// trip per exchange and one CTA barrier per step.  Every wait is bounded by a
+// global-timer limit and a shared abort flag; a CTA that gives up records
 // PAT_ERR_TIMEOUT, raises the abort flag and leaves the loop, so the launch
 // always ends.
-#include <cooperative_groups.h>
-
 #include "internal.h"
 #include "stencil.cuh"
 
 namespace pat {
 namespace {
 
+using u64 = unsigned long long;
+
 constexpr int TX = 64;
 constexpr int TY = 32;
 constexpr int NTHREADS = (TX / 4) * (TY / 2);  // 256: each thread owns 2 rows x 4 columns
 constexpr int XOFF = 8;                         // left halo columns in shared memory (>= R, multiple of 4)
 constexpr int PITCH = TX + 16;                  // 8 halo columns each side
+constexpr int RCOUNT = NTHREADS / 4;            // threads serving one neighbour
 static_assert(NTHREADS % 128 == 0, "four halo regions need whole warps");
 
-template <int R>
+template <int R, bool ADJ>
 struct Geo {
+  static constexpr int NF = ADJ ? 2 : 1;           // fields exchanged: P, or (W_hi, W_lo)
   static constexpr int ROWS = TY + 2 * R;
-  static constexpr int SBUF = ROWS * PITCH;         // one shared-memory field buffer
-  static constexpr int STRIP = 2 * R * (TX + TY);   // floats published per tile per slot
+  static constexpr int SBUF = ROWS * PITCH;        // one shared-memory field buffer
+  static constexpr int STRIP = 2 * R * (TX + TY);  // words per field per tile per slot
+  static constexpr int SLOT = NF * STRIP;
+  static constexpr int NPAIR = R * TX / 2;         // word pairs of a north/south strip
+  static constexpr int NSIDE = TY * R;             // words of a west/east strip
+  static constexpr int PER_NS = (NPAIR + RCOUNT - 1) / RCOUNT;
+  static constexpr int PER_WE = (NSIDE + RCOUNT - 1) / RCOUNT;
 };
 
-// Bounded wait until *flag >= target (wrap-safe).  Executed by a whole warp.
-__device__ __forceinline__ bool wait_flag(const int* flag, int target, const int* abort, long long timeout_ns) {
-  if (__all_sync(0xffffffffu, (int)(ld_acquire_gpu(flag) - target) >= 0)) return true;
-  const unsigned long long t0 = global_timer_ns();
+__device__ __forceinline__ u64 pack(float v, unsigned tag) {
+  return ((u64)tag << 32) | (u64)__float_as_uint(v);
+}
+__device__ __forceinline__ float unpack(u64 w) { return __uint_as_float((unsigned)(w & 0xffffffffull)); }
+__device__ __forceinline__ unsigned tag_of(u64 w) { return (unsigned)(w >> 32); }
+
+__device__ __forceinline__ void st_word2(u64* p, u64 a, u64 b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void st_word(u64* p, u64 a) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+__device__ __forceinline__ void ld_word2(const u64* p, u64& a, u64& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ u64 ld_word(const u64* p) {
+  u64 a;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(a) : "l"(p) : "memory");
+  return a;
+}
+
+// Write the thread's 2x4 block of field f of the new state into a shared
+// buffer and, tagged, into the boundary strips X: [top R x TX][bottom R x TX]
+// [left TY x R][right TY x R].
+template <int R>
+__device__ __forceinline__ void store_field(float* Sn, u64* X, const float V[2][4], int r0, int c0, unsigned tag) {
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int row = r0 + rr;
+    *reinterpret_cast<float4*>(Sn + (row + R) * PITCH + XOFF + c0) =
+        make_float4(V[rr][0], V[rr][1], V[rr][2], V[rr][3]);
+    u64* dst = nullptr;
+    if (row < R) dst = X + row * TX + c0;
+    if (row >= TY - R) dst = X + R * TX + (row - (TY - R)) * TX + c0;
+    if (dst) {  // TY >= 2R: a row is in at most one of the two strips
+      st_word2(dst, pack(V[rr][0], tag), pack(V[rr][1], tag));
+      st_word2(dst + 2, pack(V[rr][2], tag), pack(V[rr][3], tag));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + j;
+      if (col < R) st_word(X + 2 * R * TX + row * R + col, pack(V[rr][j], tag));
+      if (col >= TX - R) st_word(X + 2 * R * TX + TY * R + row * R + (col - (TX - R)), pack(V[rr][j], tag));
+    }
+  }
+}
+
+// Copy the halo of state `tag` from the neighbour's strips X (one slot, NF
+// fields) into the shared buffers at Sc (field f at Sc + f*SBUF).  Executed by
+// the RCOUNT threads of one region; returns false if the wait ran out.
+template <int R, bool ADJ>
+__device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsigned tag, const int* abort,
+                          long long timeout_ns, int poll_ns) {
+  using G = Geo<R, ADJ>;
+  const bool ns = region < 2;
+  const int per = ns ? G::PER_NS : G::PER_WE;
+  const int count = ns ? G::NPAIR : G::NSIDE;
+  unsigned pending = 0;
+  for (int f = 0; f < G::NF; ++f)
+    for (int j = 0; j < per; ++j)
+      if (rrank + j * RCOUNT < count) pending |= 1u << (f * per + j);
+  unsigned long long t0 = 0;
   for (unsigned it = 0; it < (1u << 28); ++it) {
-    if (__all_sync(0xffffffffu, (int)(ld_acquire_gpu(flag) - target) >= 0)) return true;
+    for (int f = 0; f < G::NF; ++f) {
+      float* S = Sc + f * G::SBUF;
+      const u64* Xf = X + f * G::STRIP;
+      for (int j = 0; j < per; ++j) {
+        const unsigned bit = 1u << (f * per + j);
+        if (!(pending & bit)) continue;
+        const int i = rrank + j * RCOUNT;
+        if (ns) {
+          u64 a, b;
+          ld_word2(Xf + (region == 0 ? R * TX : 0) + 2 * i, a, b);
+          if (tag_of(a) == tag && tag_of(b) == tag) {
+            const int row = (2 * i) / TX, col = (2 * i) % TX;
+            const int srow = region == 0 ? row : TY + R + row;
+            *reinterpret_cast<float2*>(S + srow * PITCH + XOFF + col) = make_float2(unpack(a), unpack(b));
+            pending &= ~bit;
+          }
+        } else {
+          const u64 a = ld_word(Xf + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
+          if (tag_of(a) == tag) {
+            const int row = i / R, jj = i % R;
+            S[(row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj)] = unpack(a);
+            pending &= ~bit;
+          }
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, pending == 0)) return true;
+    if (it == 0) t0 = global_timer_ns();
+    if (poll_ns > 0) __nanosleep(poll_ns);
     if ((it & 31u) == 31u) {
       if (ld_relaxed_gpu(abort) != 0) return false;
       if ((long long)(global_timer_ns() - t0) > timeout_ns) return false;
@@ -61,33 +163,12 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int target, const int
   return false;
 }
 
-// Write the thread's 2x4 block of the new state into a shared buffer and the
-// boundary strips of the exchange slot X: [top R x TX][bottom R x TX]
-// [left TY x R][right TY x R].
-template <int R>
-__device__ __forceinline__ void store_state(float* Sn, float* X, const float V[2][4], int r0, int c0) {
-#pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    const int row = r0 + rr;
-    const float4 v = make_float4(V[rr][0], V[rr][1], V[rr][2], V[rr][3]);
-    *reinterpret_cast<float4*>(Sn + (row + R) * PITCH + XOFF + c0) = v;
-    if (row < R) *reinterpret_cast<float4*>(X + row * TX + c0) = v;
-    if (row >= TY - R) *reinterpret_cast<float4*>(X + R * TX + (row - (TY - R)) * TX + c0) = v;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int col = c0 + j;
-      if (col < R) X[2 * R * TX + row * R + col] = V[rr][j];
-      if (col >= TX - R) X[2 * R * TX + TY * R + row * R + (col - (TX - R))] = V[rr][j];
-    }
-  }
-}
-
 template <int R, bool ADJ, bool VARC>
 __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persist2DArgs a) {
-  using G = Geo<R>;
+  using G = Geo<R, ADJ>;
   extern __shared__ float4 smem4[];
-  float* S0 = reinterpret_cast<float*>(smem4);
-  float* J = S0 + 2 * G::SBUF;  // adjoint injection accumulator, TY x TX
+  float* S0 = reinterpret_cast<float*>(smem4);  // [slot][field] buffers
+  float* J0 = S0 + 2 * G::NF * G::SBUF;         // adjoint injection accumulators, 2 x TY x TX
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -100,21 +181,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   const int c0 = (t % (TX / 4)) * 4;
   const int r0 = (t / (TX / 4)) * 2;
   const int nx = a.nx, ny = a.ny, nt = a.nt;
+  u64* xbuf = reinterpret_cast<u64*>(a.xbuf);
 
-  const unsigned ep = ld_acquire_gpu_u(a.epoch);
-  const int base = (int)(ep << 20);
+  const unsigned base = ld_acquire_gpu_u(a.epoch) << 20;
 
   // halo duty of this warp: 0 = north, 1 = south, 2 = west, 3 = east neighbour
   const int region = warp & 3;
   const int rrank = (warp >> 2) * 32 + lane;
-  constexpr int RCOUNT = NTHREADS / 4;
   int nb = -1;
   if (region == 0 && tiy > 0) nb = tile - a.tiles_x;
   if (region == 1 && tiy < a.tiles_y - 1) nb = tile + a.tiles_x;
   if (region == 2 && tix > 0) nb = tile - 1;
   if (region == 3 && tix < a.tiles_x - 1) nb = tile + 1;
 
+  // forward: P, D ; adjoint: Q (in P), G (in D) and their compensation terms
   float P[2][4], D[2][4], K[2][4];
+  float Pl[2][4], Dl[2][4], Kl[2][4];
   bool valid[2][4];
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr)
@@ -125,63 +207,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       valid[rr][j] = v;
       const long long gi = (long long)gy * nx + gx;
       K[rr][j] = v ? (VARC ? a.kappa[gi] : a.kappa0) : 0.f;
+      Kl[rr][j] = v ? (VARC ? a.kappa_lo[gi] : a.kappa0_lo) : 0.f;
       P[rr][j] = (!ADJ && v) ? a.in[gi] : 0.f;
       D[rr][j] = 0.f;
+      Pl[rr][j] = 0.f;
+      Dl[rr][j] = 0.f;
     }
-  for (int i = t; i < 2 * G::SBUF; i += NTHREADS) S0[i] = 0.f;
+  for (int i = t; i < 2 * G::NF * G::SBUF; i += NTHREADS) S0[i] = 0.f;
   if (ADJ)
-    for (int i = t; i < TX * TY; i += NTHREADS) J[i] = 0.f;
+    for (int i = t; i < 2 * TX * TY; i += NTHREADS) J0[i] = 0.f;
   if (t == 0) s_abort = 0;
   __syncthreads();
 
-  {  // publish state 0
-    float V[2][4];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) V[rr][j] = ADJ ? K[rr][j] * P[rr][j] : P[rr][j];
-    store_state<R>(S0, a.xbuf + (size_t)tile * 2 * G::STRIP, V, r0, c0);
-    __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      st_release_gpu(&a.flags[tile], base);
-    }
+  {  // publish state 0 (forward: x; adjoint: zero)
+    u64* X = xbuf + (size_t)tile * 2 * G::SLOT;
+    store_field<R>(S0, X, P, r0, c0, base);
+    if (ADJ) store_field<R>(S0 + G::SBUF, X + G::STRIP, P, r0, c0, base);
   }
 
   for (int k = 0; k < nt; ++k) {
-    float* Sc = S0 + (k & 1) * G::SBUF;
-    // ---- halo of state k from the neighbours' slot (k & 1)
+    float* Sc = S0 + (k & 1) * G::NF * G::SBUF;
+    float* Jc = J0 + (k & 1) * TX * TY;
+    // ---- halo of state k from the neighbour's slot (k & 1)
     if (nb >= 0) {
-      if (!wait_flag(&a.flags[nb], base + k, a.abort, a.timeout_ns)) {
+      const u64* X = xbuf + ((size_t)nb * 2 + (k & 1)) * G::SLOT;
+      if (!load_halo<R, ADJ>(Sc, X, region, rrank, base + (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
         if (lane == 0) {
           s_abort = 1;
           atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
           atomicExch(a.abort, 1);
-        }
-      } else {
-        const float* X = a.xbuf + ((size_t)nb * 2 + (k & 1)) * G::STRIP;
-        if (region == 0) {  // north tile's bottom strip -> my rows -R .. -1
-          for (int i = rrank; i < R * TX / 4; i += RCOUNT) {
-            const int row = i / (TX / 4), cq = (i % (TX / 4)) * 4;
-            *reinterpret_cast<float4*>(Sc + row * PITCH + XOFF + cq) =
-                __ldcg(reinterpret_cast<const float4*>(X + R * TX + row * TX + cq));
-          }
-        } else if (region == 1) {  // south tile's top strip -> my rows TY .. TY+R-1
-          for (int i = rrank; i < R * TX / 4; i += RCOUNT) {
-            const int row = i / (TX / 4), cq = (i % (TX / 4)) * 4;
-            *reinterpret_cast<float4*>(Sc + (TY + R + row) * PITCH + XOFF + cq) =
-                __ldcg(reinterpret_cast<const float4*>(X + row * TX + cq));
-          }
-        } else if (region == 2) {  // west tile's right strip -> my columns -R .. -1
-          for (int i = rrank; i < TY * R; i += RCOUNT) {
-            const int row = i / R, j = i % R;
-            Sc[(row + R) * PITCH + XOFF - R + j] = __ldcg(X + 2 * R * TX + TY * R + i);
-          }
-        } else {  // east tile's left strip -> my columns TX .. TX+R-1
-          for (int i = rrank; i < TY * R; i += RCOUNT) {
-            const int row = i / R, j = i % R;
-            Sc[(row + R) * PITCH + XOFF + TX + j] = __ldcg(X + 2 * R * TX + i);
-          }
         }
       }
     }
@@ -192,7 +246,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
         const InjCell ic = a.inj[e];
         float s = 0.f;
         for (int q = ic.beg; q < ic.end; ++q) s = fmaf(a.ent_w[q], a.in[(long long)a.ent_sensor[q] * nt + n], s);
-        J[ic.local] = s;
+        Jc[ic.local] = s;
       }
     }
     __syncthreads();
@@ -203,13 +257,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       for (int e = a.tile_samp_ptr[tile] + t; e < e1; e += NTHREADS) {
         const SampEntry se = a.samp[e];
         const float* b = Sc + (se.ly + R) * PITCH + XOFF + se.lx;
-        const float v = se.w[0] * b[0] + se.w[1] * b[1] + se.w[2] * b[PITCH] + se.w[3] * b[PITCH + 1];
-        a.out[(long long)se.sensor * nt + k] = v;
+        if (se.part < 0) {
+          const float v = se.w[0] * b[0] + se.w[1] * b[1] + se.w[2] * b[PITCH] + se.w[3] * b[PITCH + 1];
+          a.out[(long long)se.sensor * nt + k] = v;
+        } else {
+          a.part[(long long)se.part * nt + k] = se.w[0] * b[0];
+        }
       }
     }
 
     float L[2][4];
-    lap_2x4<R>(Sc, PITCH, r0 + R, XOFF + c0, a.w, L);
+    lap_2x4<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, a.w, L);
+    if (ADJ) lap_2x4<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, a.w, L);
 
     if (k == nt - 1) {
       if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L(kappa Q^1)
@@ -219,21 +278,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
           for (int j = 0; j < 4; ++j) {
             if (!valid[rr][j]) continue;
             const int lr = r0 + rr, lc = c0 + j;
-            const float xv = J[lr * TX + lc] + D[rr][j] + 0.5f * L[rr][j];
+            const float xv = Jc[lr * TX + lc] + (D[rr][j] + Dl[rr][j]) + 0.5f * L[rr][j];
             a.out[(long long)(gy0 + lr) * nx + gx0 + lc] = xv;
           }
       }
       break;
     }
 
-    float V[2][4];
+    float V[2][4], Vl[2][4];
     if (!ADJ) {
       const float cf = (k == 0) ? 0.5f : 1.0f;
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          D[rr][j] = fmaf(cf * K[rr][j], L[rr][j], D[rr][j]);
+          // D += cf (kappa_hi + kappa_lo) L
+          D[rr][j] = fmaf(cf * K[rr][j], L[rr][j], fmaf(cf * Kl[rr][j], L[rr][j], D[rr][j]));
           P[rr][j] += D[rr][j];
           V[rr][j] = P[rr][j];
         }
@@ -243,20 +303,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int li = (r0 + rr) * TX + c0 + j;
-          const float g = valid[rr][j] ? (D[rr][j] + J[li]) + L[rr][j] : 0.f;
-          J[li] = 0.f;
+          const float inc = Jc[li] + L[rr][j];
+          Jc[li] = 0.f;
+          float e;
+          float g = two_sum(D[rr][j], inc + Dl[rr][j], e);  // G += inc (compensated)
+          float gl = e;
+          float q = two_sum(P[rr][j], g, e);  // Q += G (compensated)
+          float ql = Pl[rr][j] + e;
+          if (!valid[rr][j]) g = gl = q = ql = 0.f;
           D[rr][j] = g;
-          P[rr][j] = valid[rr][j] ? P[rr][j] + g : 0.f;
-          V[rr][j] = K[rr][j] * P[rr][j];
+          Dl[rr][j] = gl;
+          P[rr][j] = q;
+          Pl[rr][j] = ql;
+          // kappa (Q + Ql) as hi + lo: exact product error plus the small cross terms
+          const float wh = K[rr][j] * q;
+          V[rr][j] = wh;
+          Vl[rr][j] = fmaf(K[rr][j], q, -wh) + fmaf(K[rr][j], ql, Kl[rr][j] * q);
         }
     }
-    store_state<R>(S0 + ((k + 1) & 1) * G::SBUF, a.xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::STRIP, V, r0,
-                   c0);
-    __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      st_release_gpu(&a.flags[tile], base + k + 1);
-    }
+    float* Sn = S0 + ((k + 1) & 1) * G::NF * G::SBUF;
+    u64* Xn = xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT;
+    const unsigned tag = base + (unsigned)(k + 1);
+    store_field<R>(Sn, Xn, V, r0, c0, tag);
+    if (ADJ) store_field<R>(Sn + G::SBUF, Xn + G::STRIP, Vl, r0, c0, tag);
   }
 
   // launch accounting: the last CTA to finish advances the epoch and clears abort
@@ -273,16 +342,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   }
 }
 
+__global__ void split_combine_kernel(const float* __restrict__ part, const int* __restrict__ split_sensor,
+                                     int nsplit, int nt, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nsplit * nt) return;
+  const int q = (int)(i / nt), t = (int)(i % nt);
+  const float* p = part + (long long)4 * q * nt + t;
+  y[(long long)split_sensor[q] * nt + t] = ((p[0] + p[nt]) + p[2 * nt]) + p[3 * nt];
+}
+
 template <int R, bool ADJ, bool VARC>
-constexpr void* kfn() {
+void* kfn() {
   return (void*)wave2d_persist_kernel<R, ADJ, VARC>;
 }
 
 void* pick(int R, bool adj, bool varc) {
-#define PAT_P2D(RR)                                                           \
-  if (R == RR) {                                                              \
-    if (adj) return varc ? kfn<RR, true, true>() : kfn<RR, true, false>();    \
-    return varc ? kfn<RR, false, true>() : kfn<RR, false, false>();           \
+#define PAT_P2D(RR)                                                       \
+  if (R == RR) {                                                          \
+    if (adj) return varc ? kfn<RR, true, true>() : kfn<RR, true, false>(); \
+    return varc ? kfn<RR, false, true>() : kfn<RR, false, false>();       \
   }
   PAT_P2D(1)
   PAT_P2D(3)
@@ -294,15 +372,31 @@ void* pick(int R, bool adj, bool varc) {
 
 size_t smem_bytes(int R, bool adj) {
   const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
-  return (2 * sbuf + (adj ? (size_t)TX * TY : 0)) * sizeof(float);
+  const size_t nf = adj ? 2 : 1;
+  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float);
+}
+
+cudaError_t prepare(void* f, int R, bool adj) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(R, adj));
 }
 
 }  // namespace
+
+cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, int nsplit, int nt, float* y,
+                                    cudaStream_t st) {
+  if (nsplit <= 0) return cudaSuccess;
+  const long long n = (long long)nsplit * nt;
+  split_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, split_sensor, nsplit, nt, y);
+  return cudaGetLastError();
+}
 
 bool persist2d_supported(int R, bool) { return R == 1 || R == 3 || R == 5 || R == 7; }
 int persist2d_tile_x() { return TX; }
 int persist2d_tile_y() { return TY; }
 size_t persist2d_smem_bytes(int R, bool adj) { return smem_bytes(R, adj); }
+size_t persist2d_xbuf_words(int R, bool adj, int ntiles) {
+  return (size_t)ntiles * 2 * (adj ? 2 : 1) * 2 * R * (TX + TY);
+}
 
 int persist2d_max_ctas(int R, bool adj, bool varc) {
   void* f = pick(R, adj, varc);
@@ -310,6 +404,7 @@ int persist2d_max_ctas(int R, bool adj, bool varc) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (prepare(f, R, adj) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj)) != cudaSuccess)
     return 0;
   return sms * per_sm;
@@ -318,6 +413,8 @@ int persist2d_max_ctas(int R, bool adj, bool varc) {
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {
   void* f = pick(R, adj, varc);
   if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = prepare(f, R, adj);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
   return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj), st);
 }

@@ -8,11 +8,14 @@
 //   adjoint  Q^n = S^T r_n + 2 Q^{n+1} - Q^{n+2} + L(kappa Q^{n+1}),
 //            x = S^T r_0 + Q^1 - Q^2 + 1/2 L(kappa Q^1)
 //
-// one kernel per step: next = c_cur cur - c_prev prev + c_lap (kappa L cur)
-// (forward) or + c_lap L(kappa cur) (adjoint).  Per point-update this reads
-// cur, prev (and kappa when the medium varies) and writes next: 12 B (16 B)
-// of compulsory traffic; halo re-reads hit L2/shared memory.  Sensor sampling
-// of `cur` is fused into the same launch.
+// 2D kernels step the increment form (D^{n+1} = D^n + kappa L P^n,
+// P^{n+1} = P^n + D^{n+1}; adjoint G/Q likewise): 16 B (20 B with a varying
+// medium) per point-update, but FP32 rounding is not amplified in the smooth
+// modes, which keeps thousands of steps within 1e-5 of FP64.  The 3D kernel
+// steps the three-level form, next = c_cur cur - c_prev prev + c_lap kappa L
+// cur: 12 B (16 B) per point-update for the HBM-bound volumes, whose step
+// counts stay in the hundreds.  Halo re-reads hit L2/shared memory.  Sensor
+// sampling of `cur` is fused into the same launch.
 #include "internal.h"
 #include "stencil.cuh"
 
@@ -33,37 +36,51 @@ constexpr int S2_TX = 64, S2_TY = 32, S2_THREADS = 256, S2_XOFF = 8, S2_PITCH = 
 
 template <int R, bool ADJ, bool VARC>
 __global__ void __launch_bounds__(S2_THREADS) step2d_kernel(const StepArgs a) {
-  __shared__ __align__(16) float S[(S2_TY + 2 * R) * S2_PITCH];
+  constexpr int NF = ADJ ? 2 : 1;  // forward: P ; adjoint: kappa*Q as hi + lo
+  constexpr int SB = (S2_TY + 2 * R) * S2_PITCH;
+  __shared__ __align__(16) float S[NF * SB];
   const int t = threadIdx.x;
   const long long bid = (long long)blockIdx.y * gridDim.x + blockIdx.x;
   fused_sample(a, bid * S2_THREADS + t);
 
   const int nx = a.nx, ny = a.ny;
   const int gx0 = blockIdx.x * S2_TX, gy0 = blockIdx.y * S2_TY;
-  // stage cur (times kappa for the adjoint of a varying medium) with halo
-  auto fetch = [&](int gx, int gy) -> float {
-    if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) return 0.f;
-    const long long gi = (long long)gy * nx + gx;
-    float v = a.cur[gi];
-    if (ADJ && VARC) v *= a.kappa[gi];
-    return v;
+  // stage the stencil input with its halo: P, or kappa (Q + Ql) split as hi + lo
+  auto stage = [&](int gx, int gy, int sidx) {
+    float hi = 0.f, lo = 0.f;
+    if (gx >= 0 && gy >= 0 && gx < nx && gy < ny) {
+      const long long gi = (long long)gy * nx + gx;
+      const float q = a.cur[gi];
+      if (ADJ) {
+        const float k = VARC ? a.kappa[gi] : a.kappa0;
+        const float kl = VARC ? a.kappa_lo[gi] : a.kappa0_lo;
+        const float ql = a.cur_lo[gi];
+        hi = k * q;
+        lo = fmaf(k, q, -hi) + fmaf(k, ql, kl * q);
+      } else {
+        hi = q;
+      }
+    }
+    S[sidx] = hi;
+    if (ADJ) S[SB + sidx] = lo;
   };
   // interior + north/south halo rows (full tile width)
   for (int i = t; i < (S2_TY + 2 * R) * S2_TX; i += S2_THREADS) {
     const int row = i / S2_TX, col = i % S2_TX;
-    S[row * S2_PITCH + S2_XOFF + col] = fetch(gx0 + col, gy0 + row - R);
+    stage(gx0 + col, gy0 + row - R, row * S2_PITCH + S2_XOFF + col);
   }
   // west/east halo columns
   for (int i = t; i < S2_TY * 2 * R; i += S2_THREADS) {
     const int row = i / (2 * R), j = i % (2 * R);
     const int col = j < R ? -R + j : S2_TX + (j - R);
-    S[(row + R) * S2_PITCH + S2_XOFF + col] = fetch(gx0 + col, gy0 + row);
+    stage(gx0 + col, gy0 + row, (row + R) * S2_PITCH + S2_XOFF + col);
   }
   __syncthreads();
 
   const int c0 = (t % (S2_TX / 4)) * 4, r0 = (t / (S2_TX / 4)) * 2;
   float L[2][4];
-  lap_2x4<R>(S, S2_PITCH, r0 + R, S2_XOFF + c0, a.w, L);
+  lap_2x4<R, true, false>(S, S2_PITCH, r0 + R, S2_XOFF + c0, a.w, L);
+  if (ADJ) lap_2x4<R, false, true>(S + SB, S2_PITCH, r0 + R, S2_XOFF + c0, a.w, L);
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
@@ -71,12 +88,27 @@ __global__ void __launch_bounds__(S2_THREADS) step2d_kernel(const StepArgs a) {
       const int gx = gx0 + c0 + j, gy = gy0 + r0 + rr;
       if (gx >= nx || gy >= ny) continue;
       const long long gi = (long long)gy * nx + gx;
-      const float cur = (ADJ && VARC) ? a.cur[gi] : S[(r0 + rr + R) * S2_PITCH + S2_XOFF + c0 + j];
-      const float kap = ADJ ? (VARC ? 1.f : a.kappa0) : (VARC ? a.kappa[gi] : a.kappa0);
-      float v = a.c_cur * cur;
-      if (a.prev) v -= a.c_prev * a.prev[gi];
-      v = fmaf(a.c_lap * kap, L[rr][j], v);
-      a.next[gi] = v;
+      if (ADJ) {
+        const float g0 = a.dbuf[gi], gl0 = a.dbuf_lo[gi];
+        if (a.final_step) {  // x = S^T r_0 (already in G) + G + 1/2 L(kappa Q^1)
+          a.next[gi] = fmaf(a.c_lap, L[rr][j], g0 + gl0);
+          continue;
+        }
+        float e;
+        const float g = two_sum(g0, L[rr][j] + gl0, e);  // G += L(kappa Q)  (compensated)
+        a.dbuf[gi] = g;
+        a.dbuf_lo[gi] = e;
+        const float q = two_sum(a.cur[gi], g, e);  // Q^n = Q^{n+1} + G  (compensated)
+        a.next[gi] = q;
+        a.next_lo[gi] = a.cur_lo[gi] + e;
+      } else {
+        const float kap = VARC ? a.kappa[gi] : a.kappa0;
+        const float kap_lo = VARC ? a.kappa_lo[gi] : a.kappa0_lo;
+        const float cur = S[(r0 + rr + R) * S2_PITCH + S2_XOFF + c0 + j];
+        const float d = fmaf(a.c_lap * kap, L[rr][j], fmaf(a.c_lap * kap_lo, L[rr][j], a.d_zero ? 0.f : a.dbuf[gi]));
+        a.dbuf[gi] = d;
+        a.next[gi] = cur + d;
+      }
     }
 }
 
@@ -180,10 +212,12 @@ __global__ void __launch_bounds__(S3_THREADS) step3d_kernel(const StepArgs a) {
         if (x >= nx) continue;
         const long long gi = (long long)z * plane + (long long)gy * nx + x;
         const float cur = (ADJ && VARC) ? a.cur[gi] : q[R][j];
+        // kappa as hi + lo (a coherent rounding of a constant kappa would drift the phase)
         const float kap = ADJ ? (VARC ? 1.f : a.kappa0) : (VARC ? a.kappa[gi] : a.kappa0);
+        const float kap_lo = ADJ ? (VARC ? 0.f : a.kappa0_lo) : (VARC ? a.kappa_lo[gi] : a.kappa0_lo);
         float v = a.c_cur * cur;
         if (a.prev) v -= a.c_prev * a.prev[gi];
-        v = fmaf(a.c_lap * kap, L[j], v);
+        v = fmaf(a.c_lap * kap, L[j], fmaf(a.c_lap * kap_lo, L[j], v));
         a.next[gi] = v;
       }
     }

@@ -32,7 +32,7 @@ def make_pair(w, path=None, level_offset=0):
     return plan, wave, wav
 
 
-def custom(shape, nt, order, varc, ns, seed, family=2, levels=1, layout="random"):
+def custom(shape, nt, order, varc, ns, seed, family=2, levels=0, layout="random"):
     """Small seeded workload of arbitrary (possibly ragged) shape."""
     rng = np.random.default_rng(seed)
     h = 1e-4
