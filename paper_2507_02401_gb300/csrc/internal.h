@@ -70,8 +70,6 @@ struct Persist2DArgs {
   const int* ent_sensor;
   const float* ent_w;
   void* xbuf;            // tagged boundary strips (64-bit words), 2 slots per tile
-  unsigned* epoch;       // launch counter (device)
-  unsigned* done;        // CTAs finished in this launch
   int* abort;            // set when any CTA gives up
   int* status;           // sticky plan status
   long long timeout_ns;  // bound on any single wait

@@ -27,13 +27,20 @@ static Persist2DArgs persist_args(pat_plan* p) {
   a.ent_sensor = p->d_ent_sensor;
   a.ent_w = p->d_ent_w;
   a.xbuf = p->d_xbuf;
-  a.epoch = p->d_epoch;
-  a.done = p->d_done;
   a.abort = p->d_abort;
   a.status = p->d_status;
   a.timeout_ns = p->timeout_ns;
   a.poll_ns = p->poll_ns;
   return a;
+}
+
+// One persistent launch: the exchange words are invalidated (no valid tag) and
+// the abort flag cleared on the stream first.
+static pat_status persist_launch(pat_plan* p, bool adj, const Persist2DArgs& a, cudaStream_t st) {
+  PAT_TRY_CUDA(cudaMemsetAsync(p->d_xbuf, 0xff, p->xbuf_bytes, st));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
+  PAT_TRY_CUDA(persist2d_launch(p->R, adj, p->varc, a, p->ntiles, st));
+  return PAT_OK;
 }
 
 static StepArgs step_args(pat_plan* p) {
@@ -79,7 +86,7 @@ static pat_status wave_forward_impl(pat_plan* p, const float* x, float* y, cudaS
     Persist2DArgs a = persist_args(p);
     a.in = x;
     a.out = y;
-    PAT_TRY_CUDA(persist2d_launch(p->R, false, p->varc, a, p->ntiles, st));
+    PAT_TRY(persist_launch(p, false, a, st));
     PAT_TRY_CUDA(persist2d_split_combine(p->d_part, p->d_split_sensor, p->nsplit, p->nt, y, st));
     return PAT_OK;
   }
@@ -125,7 +132,7 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
     Persist2DArgs a = persist_args(p);
     a.in = y;
     a.out = x;
-    PAT_TRY_CUDA(persist2d_launch(p->R, true, p->varc, a, p->ntiles, st));
+    PAT_TRY(persist_launch(p, true, a, st));
     return PAT_OK;
   }
   const int nt = p->nt;

@@ -237,19 +237,11 @@ static pat_status setup_persistent(pat_plan* p, cudaStream_t st) {
   PAT_TRY(upload(p, &p->d_samp, samp, "tile sampling entries", st));
   PAT_TRY(upload(p, &p->d_tile_inj_ptr, inj_ptr, "tile injection offsets", st));
   PAT_TRY(upload(p, &p->d_tinj, inj, "tile injection cells", st));
-  // tagged exchange words (the adjoint exchanges two fields); tags start at
-  // epoch 1 << 20, so the zeroed buffer never matches
-  const size_t words = persist2d_xbuf_words(p->R, true, p->ntiles);
-  PAT_TRY(plan_alloc(p, &p->d_xbuf, words * 8, "exchange strips"));
+  // tagged exchange words, invalidated (0xff bytes) before every launch
+  p->xbuf_bytes = persist2d_xbuf_words(p->R, true, p->ntiles) * 8;
+  PAT_TRY(plan_alloc(p, &p->d_xbuf, p->xbuf_bytes, "exchange strips"));
   if (const char* e = getenv("PAT_POLL_NS")) p->poll_ns = std::max(0, atoi(e));
-  PAT_TRY(alloc_n(p, &p->d_epoch, 1, "epoch"));
-  PAT_TRY(alloc_n(p, &p->d_done, 1, "done counter"));
   PAT_TRY(alloc_n(p, &p->d_abort, 1, "abort flag"));
-  const unsigned one = 1u;
-  PAT_TRY_CUDA(cudaMemcpyAsync(p->d_epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice, st));
-  PAT_TRY_CUDA(cudaMemsetAsync(p->d_done, 0, sizeof(unsigned), st));
-  PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
-  PAT_TRY_CUDA(cudaMemsetAsync(p->d_xbuf, 0, words * 8, st));
   return PAT_OK;
 }
 

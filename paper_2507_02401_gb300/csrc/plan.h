@@ -48,8 +48,7 @@ struct pat_plan {
   int* d_tile_inj_ptr = nullptr;
   pat::InjCell* d_tinj = nullptr;
   void* d_xbuf = nullptr;  // tagged 64-bit exchange words
-  unsigned* d_epoch = nullptr;
-  unsigned* d_done = nullptr;
+  size_t xbuf_bytes = 0;
   int* d_abort = nullptr;
   long long timeout_ns = 2000000000LL;
   int poll_ns = 0;  // exchange polling back-off

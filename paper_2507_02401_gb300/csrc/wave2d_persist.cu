@@ -52,29 +52,49 @@ static_assert(NTHREADS % 128 == 0, "four halo regions need whole warps");
 
 template <int R, bool ADJ>
 struct Geo {
-  static constexpr int NF = ADJ ? 2 : 1;           // fields exchanged: P, or (W_hi, W_lo)
+  static constexpr int NF = ADJ ? 2 : 1;           // shared-memory fields: P, or (W_hi, W_lo)
   static constexpr int ROWS = TY + 2 * R;
   static constexpr int SBUF = ROWS * PITCH;        // one shared-memory field buffer
-  static constexpr int STRIP = 2 * R * (TX + TY);  // words per field per tile per slot
-  static constexpr int SLOT = NF * STRIP;
+  static constexpr int STRIP = 2 * R * (TX + TY);  // exchanged words per tile per slot
+  static constexpr int SLOT = STRIP;
   static constexpr int NPAIR = R * TX / 2;         // word pairs of a north/south strip
   static constexpr int NSIDE = TY * R;             // words of a west/east strip
   static constexpr int PER_NS = (NPAIR + RCOUNT - 1) / RCOUNT;
   static constexpr int PER_WE = (NSIDE + RCOUNT - 1) / RCOUNT;
 };
 
-__device__ __forceinline__ u64 pack(float v, unsigned tag) {
-  return ((u64)tag << 32) | (u64)__float_as_uint(v);
+// Exchange words.  The buffer is filled with 0xff bytes before every launch,
+// so no stale word can carry a valid tag.
+//   forward: [step (32 bits)][P (32 bits)]
+//   adjoint: [W_lo with its low 8 mantissa bits replaced by step mod 128][W_hi]
+//            (W_lo is a correction ~2^-24 of W_hi; dropping 8 of its bits is
+//            far below FP32 rounding of W)
+template <bool ADJ>
+__device__ __forceinline__ u64 pack(float hi, float lo, unsigned step) {
+  if (!ADJ) return ((u64)step << 32) | (u64)__float_as_uint(hi);
+  const unsigned l = (__float_as_uint(lo) & ~0xffu) | (step & 0x7fu);
+  return ((u64)l << 32) | (u64)__float_as_uint(hi);
 }
-__device__ __forceinline__ float unpack(u64 w) { return __uint_as_float((unsigned)(w & 0xffffffffull)); }
-__device__ __forceinline__ unsigned tag_of(u64 w) { return (unsigned)(w >> 32); }
+template <bool ADJ>
+__device__ __forceinline__ bool tag_ok(u64 w, unsigned step) {
+  const unsigned h = (unsigned)(w >> 32);
+  return ADJ ? (h & 0xffu) == (step & 0x7fu) : h == step;
+}
+__device__ __forceinline__ float word_hi(u64 w) { return __uint_as_float((unsigned)(w & 0xffffffffull)); }
+__device__ __forceinline__ float word_lo(u64 w) { return __uint_as_float((unsigned)(w >> 32) & ~0xffu); }
 
-__device__ __forceinline__ void st_word2(u64* p, u64 a, u64 b) {
-  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+// TMA bulk copy of a shared-memory segment to global memory (async proxy).
+__device__ __forceinline__ void bulk_store(u64* gdst, const u64* ssrc, unsigned bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(sa), "r"(bytes)
+               : "memory");
 }
-__device__ __forceinline__ void st_word(u64* p, u64 a) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
-}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most one committed group is still reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void ld_word2(const u64* p, u64& a, u64& b) {
   asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
@@ -84,71 +104,101 @@ __device__ __forceinline__ u64 ld_word(const u64* p) {
   return a;
 }
 
-// Write the thread's 2x4 block of field f of the new state into a shared
-// buffer and, tagged, into the boundary strips X: [top R x TX][bottom R x TX]
-// [left TY x R][right TY x R].
-template <int R>
-__device__ __forceinline__ void store_field(float* Sn, u64* X, const float V[2][4], int r0, int c0, unsigned tag) {
+// Write the thread's 2x4 block of the new state into the shared field
+// buffer(s) Sn (second field at Sn + SBUF) and, packed and tagged, into the
+// shared outbox O laid out like the boundary strips:
+// [top R x TX][bottom R x TX][left TY x R][right TY x R].
+template <int R, bool ADJ>
+__device__ __forceinline__ void store_state(float* Sn, u64* O, const float V[2][4], const float Vl[2][4], int r0,
+                                            int c0, unsigned step) {
+  constexpr int SBUF = Geo<R, ADJ>::SBUF;
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr) {
     const int row = r0 + rr;
     *reinterpret_cast<float4*>(Sn + (row + R) * PITCH + XOFF + c0) =
         make_float4(V[rr][0], V[rr][1], V[rr][2], V[rr][3]);
+    if (ADJ)
+      *reinterpret_cast<float4*>(Sn + SBUF + (row + R) * PITCH + XOFF + c0) =
+          make_float4(Vl[rr][0], Vl[rr][1], Vl[rr][2], Vl[rr][3]);
+    u64 w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = pack<ADJ>(V[rr][j], Vl[rr][j], step);
     u64* dst = nullptr;
-    if (row < R) dst = X + row * TX + c0;
-    if (row >= TY - R) dst = X + R * TX + (row - (TY - R)) * TX + c0;
+    if (row < R) dst = O + row * TX + c0;
+    if (row >= TY - R) dst = O + R * TX + (row - (TY - R)) * TX + c0;
     if (dst) {  // TY >= 2R: a row is in at most one of the two strips
-      st_word2(dst, pack(V[rr][0], tag), pack(V[rr][1], tag));
-      st_word2(dst + 2, pack(V[rr][2], tag), pack(V[rr][3], tag));
+      *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(w[0], w[1]);
+      *reinterpret_cast<ulonglong2*>(dst + 2) = make_ulonglong2(w[2], w[3]);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = c0 + j;
-      if (col < R) st_word(X + 2 * R * TX + row * R + col, pack(V[rr][j], tag));
-      if (col >= TX - R) st_word(X + 2 * R * TX + TY * R + row * R + (col - (TX - R)), pack(V[rr][j], tag));
+      if (col < R) O[2 * R * TX + row * R + col] = w[j];
+      if (col >= TX - R) O[2 * R * TX + TY * R + row * R + (col - (TX - R))] = w[j];
     }
   }
 }
 
-// Copy the halo of state `tag` from the neighbour's strips X (one slot, NF
-// fields) into the shared buffers at Sc (field f at Sc + f*SBUF).  Executed by
-// the RCOUNT threads of one region; returns false if the wait ran out.
+// Hand the warp's rows [4w, 4w+4) of the outbox to the TMA engine: up to four
+// contiguous segments (top, bottom, left, right strips).
+// All lanes must have written their words; lane 0 issues and commits.
+template <int R>
+__device__ __forceinline__ void publish_warp(u64* X, const u64* O, int warp, int lane) {
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane != 0) return;
+  const int w4 = 4 * warp;
+  {
+    const int fo = 0;
+    const int tlo = w4, thi = min(w4 + 4, R);
+    if (tlo < thi) bulk_store(X + fo + tlo * TX, O + fo + tlo * TX, (unsigned)((thi - tlo) * TX * 8));
+    const int blo = max(w4, TY - R), bhi = w4 + 4;
+    if (blo < bhi)
+      bulk_store(X + fo + R * TX + (blo - (TY - R)) * TX, O + fo + R * TX + (blo - (TY - R)) * TX,
+                 (unsigned)((bhi - blo) * TX * 8));
+    bulk_store(X + fo + 2 * R * TX + w4 * R, O + fo + 2 * R * TX + w4 * R, (unsigned)(4 * R * 8));
+    bulk_store(X + fo + 2 * R * TX + TY * R + w4 * R, O + fo + 2 * R * TX + TY * R + w4 * R, (unsigned)(4 * R * 8));
+  }
+  bulk_commit();
+}
+
+// Copy the halo of state `step` from the neighbour's strips X into the shared
+// buffers at Sc (second field at Sc + SBUF).  Executed by the RCOUNT threads
+// of one region; returns false if the wait ran out.
 template <int R, bool ADJ>
-__device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsigned tag, const int* abort,
+__device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsigned step, const int* abort,
                           long long timeout_ns, int poll_ns) {
   using G = Geo<R, ADJ>;
   const bool ns = region < 2;
   const int per = ns ? G::PER_NS : G::PER_WE;
   const int count = ns ? G::NPAIR : G::NSIDE;
   unsigned pending = 0;
-  for (int f = 0; f < G::NF; ++f)
-    for (int j = 0; j < per; ++j)
-      if (rrank + j * RCOUNT < count) pending |= 1u << (f * per + j);
+  for (int j = 0; j < per; ++j)
+    if (rrank + j * RCOUNT < count) pending |= 1u << j;
   unsigned long long t0 = 0;
   for (unsigned it = 0; it < (1u << 28); ++it) {
-    for (int f = 0; f < G::NF; ++f) {
-      float* S = Sc + f * G::SBUF;
-      const u64* Xf = X + f * G::STRIP;
-      for (int j = 0; j < per; ++j) {
-        const unsigned bit = 1u << (f * per + j);
-        if (!(pending & bit)) continue;
-        const int i = rrank + j * RCOUNT;
-        if (ns) {
-          u64 a, b;
-          ld_word2(Xf + (region == 0 ? R * TX : 0) + 2 * i, a, b);
-          if (tag_of(a) == tag && tag_of(b) == tag) {
-            const int row = (2 * i) / TX, col = (2 * i) % TX;
-            const int srow = region == 0 ? row : TY + R + row;
-            *reinterpret_cast<float2*>(S + srow * PITCH + XOFF + col) = make_float2(unpack(a), unpack(b));
-            pending &= ~bit;
-          }
-        } else {
-          const u64 a = ld_word(Xf + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
-          if (tag_of(a) == tag) {
-            const int row = i / R, jj = i % R;
-            S[(row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj)] = unpack(a);
-            pending &= ~bit;
-          }
+    for (int j = 0; j < per; ++j) {
+      const unsigned bit = 1u << j;
+      if (!(pending & bit)) continue;
+      const int i = rrank + j * RCOUNT;
+      if (ns) {
+        u64 a, b;
+        ld_word2(X + (region == 0 ? R * TX : 0) + 2 * i, a, b);
+        if (tag_ok<ADJ>(a, step) && tag_ok<ADJ>(b, step)) {
+          const int row = (2 * i) / TX, col = (2 * i) % TX;
+          const int o = (region == 0 ? row : TY + R + row) * PITCH + XOFF + col;
+          *reinterpret_cast<float2*>(Sc + o) = make_float2(word_hi(a), word_hi(b));
+          if (ADJ) *reinterpret_cast<float2*>(Sc + G::SBUF + o) = make_float2(word_lo(a), word_lo(b));
+          pending &= ~bit;
+        }
+      } else {
+        const u64 a = ld_word(X + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
+        if (tag_ok<ADJ>(a, step)) {
+          const int row = i / R, jj = i % R;
+          const int o = (row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj);
+          Sc[o] = word_hi(a);
+          if (ADJ) Sc[G::SBUF + o] = word_lo(a);
+          pending &= ~bit;
         }
       }
     }
@@ -169,6 +219,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   extern __shared__ float4 smem4[];
   float* S0 = reinterpret_cast<float*>(smem4);  // [slot][field] buffers
   float* J0 = S0 + 2 * G::NF * G::SBUF;         // adjoint injection accumulators, 2 x TY x TX
+  u64* OB = reinterpret_cast<u64*>(J0 + (ADJ ? 2 * TX * TY : 0));  // outbox, 2 parities x SLOT words
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -182,8 +233,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   const int r0 = (t / (TX / 4)) * 2;
   const int nx = a.nx, ny = a.ny, nt = a.nt;
   u64* xbuf = reinterpret_cast<u64*>(a.xbuf);
-
-  const unsigned base = ld_acquire_gpu_u(a.epoch) << 20;
 
   // halo duty of this warp: 0 = north, 1 = south, 2 = west, 3 = east neighbour
   const int region = warp & 3;
@@ -220,9 +269,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   __syncthreads();
 
   {  // publish state 0 (forward: x; adjoint: zero)
-    u64* X = xbuf + (size_t)tile * 2 * G::SLOT;
-    store_field<R>(S0, X, P, r0, c0, base);
-    if (ADJ) store_field<R>(S0 + G::SBUF, X + G::STRIP, P, r0, c0, base);
+    store_state<R, ADJ>(S0, OB, P, Pl, r0, c0, 0u);
+    publish_warp<R>(xbuf + (size_t)tile * 2 * G::SLOT, OB, warp, lane);
   }
 
   for (int k = 0; k < nt; ++k) {
@@ -231,7 +279,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
     // ---- halo of state k from the neighbour's slot (k & 1)
     if (nb >= 0) {
       const u64* X = xbuf + ((size_t)nb * 2 + (k & 1)) * G::SLOT;
-      if (!load_halo<R, ADJ>(Sc, X, region, rrank, base + (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
+      if (!load_halo<R, ADJ>(Sc, X, region, rrank, (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
         if (lane == 0) {
           s_abort = 1;
           atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -292,10 +340,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          // D += cf (kappa_hi + kappa_lo) L
-          D[rr][j] = fmaf(cf * K[rr][j], L[rr][j], fmaf(cf * Kl[rr][j], L[rr][j], D[rr][j]));
+          // D += cf (kappa_hi + kappa_lo) L, the product rounded once before it meets D
+          D[rr][j] += fmaf(cf * K[rr][j], L[rr][j], (cf * Kl[rr][j]) * L[rr][j]);
           P[rr][j] += D[rr][j];
           V[rr][j] = P[rr][j];
+          Vl[rr][j] = 0.f;
         }
     } else {
 #pragma unroll
@@ -322,24 +371,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
         }
     }
     float* Sn = S0 + ((k + 1) & 1) * G::NF * G::SBUF;
-    u64* Xn = xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT;
-    const unsigned tag = base + (unsigned)(k + 1);
-    store_field<R>(Sn, Xn, V, r0, c0, tag);
-    if (ADJ) store_field<R>(Sn + G::SBUF, Xn + G::STRIP, Vl, r0, c0, tag);
+    u64* On = OB + ((k + 1) & 1) * G::SLOT;
+    if (lane == 0) bulk_wait_read_1();  // the copy that last read this outbox half is done
+    __syncwarp();
+    store_state<R, ADJ>(Sn, On, V, Vl, r0, c0, (unsigned)(k + 1));
+    publish_warp<R>(xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT, On, warp, lane);
   }
+  if (lane == 0) bulk_wait_all();
 
-  // launch accounting: the last CTA to finish advances the epoch and clears abort
-  __syncthreads();
-  if (t == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(a.done, 1u);
-    if (prev == gridDim.x - 1) {
-      *a.done = 0u;
-      atomicExch(a.abort, 0);
-      __threadfence();
-      atomicAdd(a.epoch, 1u);
-    }
-  }
 }
 
 __global__ void split_combine_kernel(const float* __restrict__ part, const int* __restrict__ split_sensor,
@@ -373,7 +412,8 @@ void* pick(int R, bool adj, bool varc) {
 size_t smem_bytes(int R, bool adj) {
   const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
   const size_t nf = adj ? 2 : 1;
-  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float);
+  const size_t outbox = 2 * (size_t)(2 * R * (TX + TY)) * sizeof(unsigned long long);
+  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float) + outbox;
 }
 
 cudaError_t prepare(void* f, int R, bool adj) {
@@ -394,9 +434,7 @@ bool persist2d_supported(int R, bool) { return R == 1 || R == 3 || R == 5 || R =
 int persist2d_tile_x() { return TX; }
 int persist2d_tile_y() { return TY; }
 size_t persist2d_smem_bytes(int R, bool adj) { return smem_bytes(R, adj); }
-size_t persist2d_xbuf_words(int R, bool adj, int ntiles) {
-  return (size_t)ntiles * 2 * (adj ? 2 : 1) * 2 * R * (TX + TY);
-}
+size_t persist2d_xbuf_words(int R, bool, int ntiles) { return (size_t)ntiles * 2 * 2 * R * (TX + TY); }
 
 int persist2d_max_ctas(int R, bool adj, bool varc) {
   void* f = pick(R, adj, varc);

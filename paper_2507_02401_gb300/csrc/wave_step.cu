@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(S2_THREADS) step2d_kernel(const StepArgs a) {
         const float kap = VARC ? a.kappa[gi] : a.kappa0;
         const float kap_lo = VARC ? a.kappa_lo[gi] : a.kappa0_lo;
         const float cur = S[(r0 + rr + R) * S2_PITCH + S2_XOFF + c0 + j];
-        const float d = fmaf(a.c_lap * kap, L[rr][j], fmaf(a.c_lap * kap_lo, L[rr][j], a.d_zero ? 0.f : a.dbuf[gi]));
+        // (kappa_hi + kappa_lo) L rounded once, before it meets the much larger increment
+        const float inc = fmaf(a.c_lap * kap, L[rr][j], (a.c_lap * kap_lo) * L[rr][j]);
+        const float d = (a.d_zero ? 0.f : a.dbuf[gi]) + inc;
         a.dbuf[gi] = d;
         a.next[gi] = cur + d;
       }
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(S3_THREADS) step3d_kernel(const StepArgs a) {
         const float kap_lo = ADJ ? (VARC ? 0.f : a.kappa0_lo) : (VARC ? a.kappa_lo[gi] : a.kappa0_lo);
         float v = a.c_cur * cur;
         if (a.prev) v -= a.c_prev * a.prev[gi];
-        v = fmaf(a.c_lap * kap, L[j], fmaf(a.c_lap * kap_lo, L[j], v));
+        v += fmaf(a.c_lap * kap, L[j], (a.c_lap * kap_lo) * L[j]);
         a.next[gi] = v;
       }
     }
