@@ -197,6 +197,32 @@ pat_status pat_plan_profile(pat_plan* plan, int enable);
 pat_status pat_plan_profile_read(pat_plan* plan, long long* kernels, int* wave_calls, double* wave_ms,
                                  long long* point_updates);
 
+/*
+ * pat_EsT_noalloc — u = E_s* x for a 2D image, with no device allocation at
+ * all.  The paper has no counterpart: this is a deployment form of pat_EsT
+ * for callers that cannot allocate device memory (a real-time loop that must
+ * not pay cudaMalloc's implicit synchronisation, a plug-in whose host
+ * application owns the device memory, a fixed up-front memory budget), and
+ * so cannot create a plan.
+ *   nx, ny        grid extents; nx * ny <= 2^20 cells (e.g. 1024 x 1024),
+ *                 both divisible by 2^levels.  Larger grids are rejected with
+ *                 PAT_ERR_INVALID and a message naming the limit.
+ *   family, levels, level_offset, s   as for pat_plan_create / pat_EsT.
+ *   x             device array of nx*ny floats (row-major, x fastest).
+ *   u             device array of nx*ny floats, coefficient layout of pat_EsT.
+ *   stream        cudaStream_t (asynchronous, like pat_EsT).
+ * The transform's scratch (2 MiB) is a fixed array in device memory that
+ * every device loading the library holds until the process exits.  The first
+ * call on a device looks up that array's address (once per device, with the
+ * device current); make that first call before starting any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (two streams,
+ * two host threads) race and corrupt each other's results, so serialise them.
+ * Nothing in the array needs to start at zero: every call writes each scratch
+ * element before reading it.
+ */
+pat_status pat_EsT_noalloc(int nx, int ny, int family, int levels, int level_offset, double s, const float* x,
+                           float* u, void* stream);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* pat_last_error(void);
 

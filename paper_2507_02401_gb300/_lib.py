@@ -51,6 +51,7 @@ SIGNATURES = [
     ("pat_plan_profile", c_int, [c_void_p, c_int]),
     ("pat_plan_profile_read", c_int, [c_void_p, ctypes.POINTER(c_longlong), ctypes.POINTER(c_int),
                                       ctypes.POINTER(c_double), ctypes.POINTER(c_longlong)]),
+    ("pat_EsT_noalloc", c_int, [c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_void_p, c_void_p]),
     ("pat_last_error", ctypes.c_char_p, []),
 ]
 
@@ -197,6 +198,12 @@ def pat_plan_profile_read(plan):
     _check(load().pat_plan_profile_read(plan, ctypes.byref(k), ctypes.byref(calls), ctypes.byref(ms),
                                         ctypes.byref(pts)))
     return k.value, calls.value, ms.value, pts.value
+
+
+def pat_EsT_noalloc(nx, ny, family, levels, level_offset, s, x, u, stream=None):
+    """E_s* of a 2D image without any device allocation (device arrays only)."""
+    return _check(load().pat_EsT_noalloc(int(nx), int(ny), int(family), int(levels), int(level_offset), float(s),
+                                         ptr(x), ptr(u), stream_handle(stream)))
 
 
 def pat_last_error():

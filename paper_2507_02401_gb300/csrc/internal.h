@@ -15,6 +15,11 @@ constexpr int kMaxR = 7;       // composed stencil radius of order 8
 constexpr int kMaxTaps = 8;    // db4 filter length
 constexpr int kMaxLevels = 20;
 
+// Orthonormal Daubechies scaling filter with nv vanishing moments (2 nv taps);
+// false if its orthonormality self-check fails.  Host code, no allocation
+// on the device.
+bool daubechies_filter(int nv, double* h);
+
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
 pat_status cuda_fail(cudaError_t e, const char* what);

@@ -93,7 +93,7 @@ static void composed_weights(int M, double* w) {
 // give the extra zeros z of H(z) = sum h_k z^k through y = (2 - z - 1/z)/4,
 // taking the root outside the unit circle; H(z) = (1+z)^nv prod (z - z_r),
 // normalised to sum h = sqrt 2.  Roots by Durand-Kerner iteration.
-static bool daubechies(int nv, double* h) {
+bool daubechies_filter(int nv, double* h) {
   using cd = std::complex<double>;
   if (nv == 1) {
     h[0] = h[1] = std::sqrt(0.5);
@@ -420,7 +420,7 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   p->levels = wav->levels;
   p->level_offset = wav->level_offset;
   double hd[kMaxTaps];
-  if (!daubechies(wav->family, hd)) {
+  if (!daubechies_filter(wav->family, hd)) {
     set_error("Daubechies filter construction failed its orthonormality check");
     return PAT_ERR_INVALID;
   }
