@@ -323,6 +323,80 @@ int oracle_adjoint(int dim, const int* n, double h, double dt, int nt, int order
   return 0;
 }
 
+/* Medium gradient: g = d<r, K x>/d kappa per cell, kappa = (c dt/h)^2.
+ *
+ * kappa enters the program only through b = c^2 dt / h = kappa h / dt in
+ * P^n = P^{n-1} + b .* (G^T v^{n-1/2}).  Reversing the program as in
+ * oracle_adjoint while also collecting the explicit dependence on b gives
+ *   d<r, y>/db = sum_{n=1}^{nt-1} Pbar^n .* (G^T v^{n-1/2}),
+ * with Pbar^n the adjoint of P^n at the point of that update; then
+ * d/dkappa = (h/dt) d/db.  The velocities v^{n-1/2} of the forward run are
+ * kept in memory (small problems only). */
+int oracle_kappa_grad(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
+                      const double* sensors, const double* x, const double* r, double* g) {
+  problem pb;
+  int rc = problem_init(&pb, dim, n, h, dt, nt, order, c, ns, sensors);
+  if (rc) {
+    problem_free(&pb);
+    return rc;
+  }
+  const geom* gm = &pb.g;
+  const long total = gm->total;
+  /* forward run, storing G^T v^{n-1/2} (on cells) for n = 1..nt-1 */
+  double* P = (double*)calloc((size_t)total, sizeof(double));
+  double* V[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) V[a] = (double*)calloc((size_t)total, sizeof(double));
+  double* GTv = (double*)calloc((size_t)total * (nt > 1 ? nt : 1), sizeof(double));
+  to_padded(gm, x, P);
+  for (int a = 0; a < dim; ++a) grad_axis(gm, a, P, V[a], -0.5 * dt / h);
+  for (int step = 1; step < nt; ++step) {
+    double* gtv = GTv + (long)step * total;
+    for (int a = 0; a < dim; ++a) gradT_axis(gm, a, V[a], gtv, 1.0);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < total; ++i) P[i] += pb.b[i] * gtv[i];
+    if (step < nt - 1)
+      for (int a = 0; a < dim; ++a) grad_axis(gm, a, P, V[a], -dt / h);
+  }
+  /* reverse sweep (as oracle_adjoint) with the explicit b-derivative */
+  double* Pb = (double*)calloc((size_t)total, sizeof(double));
+  double* bP = (double*)calloc((size_t)total, sizeof(double));
+  double* tmp = (double*)calloc((size_t)total, sizeof(double));
+  double* gb = (double*)calloc((size_t)total, sizeof(double));
+  double* Vb[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) Vb[a] = (double*)calloc((size_t)total, sizeof(double));
+  for (int step = nt - 1; step >= 1; --step) {
+    if (step < nt - 1) {
+      memset(tmp, 0, sizeof(double) * total);
+      for (int a = 0; a < dim; ++a) gradT_axis(gm, a, Vb[a], tmp, 1.0);
+#pragma omp parallel for schedule(static)
+      for (long i = 0; i < total; ++i) Pb[i] -= (dt / h) * tmp[i];
+    }
+    inject(&pb, r, Pb, step);
+    const double* gtv = GTv + (long)step * total;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < total; ++i) {
+      gb[i] += Pb[i] * gtv[i];
+      bP[i] = pb.b[i] * Pb[i];
+    }
+    for (int a = 0; a < dim; ++a) grad_axis(gm, a, bP, Vb[a], 1.0);
+  }
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < total; ++i) gb[i] *= h / dt;
+  from_padded(gm, gb, g);
+  for (int a = 0; a < dim; ++a) {
+    free(V[a]);
+    free(Vb[a]);
+  }
+  free(P);
+  free(GTv);
+  free(Pb);
+  free(bP);
+  free(tmp);
+  free(gb);
+  problem_free(&pb);
+  return 0;
+}
+
 /* Full wavefield history for small problems: P^n for n = 0..nt-1 into
  * hist[n*N + cell].  Used by the energy and closed-form checks. */
 int oracle_forward_history(int dim, const int* n, double h, double dt, int nt, int order, const double* c,

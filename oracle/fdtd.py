@@ -29,6 +29,8 @@ def _load():
         _lib.oracle_forward_history.argtypes = [ctypes.c_int, ip, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_int, dp, dp, dp]
         _lib.oracle_forward_history.restype = ctypes.c_int
+        _lib.oracle_kappa_grad.argtypes = sig + [dp]
+        _lib.oracle_kappa_grad.restype = ctypes.c_int
         _lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib.oracle_max_threads.restype = ctypes.c_int
     return _lib
@@ -90,6 +92,16 @@ class Wave:
             raise ValueError(f"oracle_adjoint failed ({rc})")
         self.evaluations += 1
         return x
+
+    def kappa_grad(self, x, r):
+        """g = d<r, K x>/d kappa per cell, kappa = (c dt / h)^2 (shape `shape`)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(self.shape))
+        r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(self.ns, self.nt))
+        g = np.zeros(self.shape, dtype=np.float64)
+        rc = _load().oracle_kappa_grad(*self._args(), _dp(x), _dp(r), _dp(g))
+        if rc != 0:
+            raise ValueError(f"oracle_kappa_grad failed ({rc})")
+        return g
 
     def history(self, x):
         """All pressure fields P^0..P^{nt-1}, shape (nt,) + shape."""

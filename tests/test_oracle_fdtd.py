@@ -248,3 +248,29 @@ def test_blowup_above_cfl():
     x = np.random.default_rng(1).standard_normal(shape)
     hist = Wave(shape, h, dt, 600, 4, 1500.0, np.zeros((0, 2))).history(x)
     assert np.abs(hist[-1]).max() > 1e3 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("shape,order", [((14, 17), 2), ((16, 12), 8), ((8, 9, 10), 4)])
+def test_kappa_grad_matches_finite_differences(shape, order):
+    """d<r, K x>/d kappa from the reverse sweep against central differences of
+    the FP64 forward map under kappa -> kappa + eps delta (kappa = (c dt/h)^2)."""
+    rng = np.random.default_rng(40 + order)
+    h = 1e-4
+    c = 1450 + 100 * rng.random(shape)
+    dt = 0.3 * h / 1600.0
+    nt = 45
+    sens = np.stack([rng.uniform(0, (s - 1) * h, 6) for s in shape[::-1]], axis=1)
+    x = rng.standard_normal(shape)
+    r = rng.standard_normal((6, nt))
+    g = Wave(shape, h, dt, nt, order, c, sens).kappa_grad(x, r)
+    kap = (c * dt / h) ** 2
+    for trial in range(3):
+        delta = kap * 1e-3 * rng.standard_normal(shape)
+        eps = 1e-3
+
+        def J(k):
+            cc = np.sqrt(k) * h / dt
+            return float(np.sum(r * Wave(shape, h, dt, nt, order, cc, sens).forward(x)))
+
+        fd = (J(kap + eps * delta) - J(kap - eps * delta)) / (2 * eps)
+        assert abs(fd - float(np.sum(g * delta))) <= 1e-7 * np.linalg.norm(g) * np.linalg.norm(delta) + 1e-12 * abs(fd)
