@@ -161,6 +161,23 @@ pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* 
                              const double* ss, int iters, float* const* xs, pat_status* per_inst, void* stream);
 
 /*
+ * pat_grad_kappa — g = d<r, K x>/d kappa per cell, kappa = (c dt / h)^2: the
+ * sensitivity of the measurements to the medium, e.g. the gradient of
+ * J = 1/2 ||K x - y||^2 with r = K x - y (chain rule for c: dkappa/dc =
+ * 2 kappa / c).  Not in the paper (its medium is known); used to
+ * differentiate K with respect to c.  With the three-level form
+ * P^{n+1} = 2P^n - P^{n-1} + kappa .* L P^n and adjoint states Q^n of K*r:
+ *   g = sum_{n=1}^{nt-2} Q^{n+1} .* L P^n + 1/2 Q^1 .* L P^0.
+ * The forward fields are needed in reverse order: the forward run keeps its
+ * restart state every `segment` steps (0 = ceil(sqrt(nt))) and each segment is
+ * recomputed when the adjoint reaches it.  Runs on the per-step engine.
+ *   x  N floats;  r  ns*nt floats;  g  N floats (output).
+ * Memory: (2 ceil((nt-1)/segment) + segment + 3) N floats + N doubles,
+ * allocated by the first call and kept by the plan (PAT_ERR_OOM if absent).
+ */
+pat_status pat_grad_kappa(pat_plan* plan, const float* x, const float* r, float* g, int segment, void* stream);
+
+/*
  * pat_plan_check — synchronises `stream`, returns and clears the plan's
  * device-side status (PAT_OK, PAT_ERR_TIMEOUT or PAT_ERR_BREAKDOWN), or
  * PAT_ERR_CUDA if the stream reports an error.

@@ -44,6 +44,7 @@ SIGNATURES = [
                           c_void_p]),
     ("pat_solve_batched", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p]),
+    ("pat_grad_kappa", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("pat_plan_check", c_int, [c_void_p, c_void_p]),
     ("pat_plan_set_path", c_int, [c_void_p, c_int]),
     ("pat_plan_get_path", c_int, [c_void_p, ctypes.POINTER(c_int)]),
@@ -167,6 +168,10 @@ def pat_solve_batched(plans, ys, alphas, ss, iters, xs, stream=None):
     st = (c_int * B)()
     rc = load().pat_solve_batched(P, B, Y, A, S, int(iters), X, st, stream_handle(stream))
     return rc, [int(v) for v in st]
+
+
+def pat_grad_kappa(plan, x, r, g, segment=0, stream=None):
+    return _check(load().pat_grad_kappa(plan, ptr(x), ptr(r), ptr(g), int(segment), stream_handle(stream)))
 
 
 def pat_plan_check(plan, stream=None):

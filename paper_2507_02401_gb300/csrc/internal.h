@@ -133,6 +133,10 @@ cudaError_t sample_launch(const float* P, int ns, int nt, int t, const int* cell
                           float* y, cudaStream_t st);
 cudaError_t inject_launch(float* Q, int n_inj, const int* inj_cell, const int* inj_ptr, const int* ent_sensor,
                           const float* ent_w, const float* r, int nt, int t, float scale, cudaStream_t st);
+cudaError_t grad_acc_launch(int R, double* gacc, const float* Q, const float* Qlo, const float* P, float coef,
+                            const StepArgs& a, int dim, cudaStream_t st);
+cudaError_t d2f_launch(float* out, const double* in, long long n, cudaStream_t st);
+cudaError_t dfill_launch(double* p, long long n, cudaStream_t st);
 cudaError_t fill_launch(float* p, long long n, float v, cudaStream_t st);
 cudaError_t copy_launch(float* dst, const float* src, long long n, cudaStream_t st);
 

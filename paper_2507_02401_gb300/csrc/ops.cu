@@ -337,6 +337,188 @@ pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_
   return PAT_OK;
 }
 
+// ------------------------------------------------------- medium gradient
+// g = d<r, K x>/d kappa with sqrt(nt)-style checkpointing: the forward run
+// keeps the restart state every C steps, the adjoint runs backwards and, for
+// each segment it reaches, the segment's fields are recomputed from its
+// checkpoint so that L P^n is available in reverse order.
+static void kg_free(pat_plan* p) {
+  cudaFree(p->kg_ckpt);
+  cudaFree(p->kg_seg);
+  cudaFree(p->kg_work);
+  cudaFree(p->kg_acc);
+  p->kg_ckpt = p->kg_seg = p->kg_work = nullptr;
+  p->kg_acc = nullptr;
+  p->kg_segment = 0;
+}
+
+static pat_status kg_alloc(pat_plan* p, int C, int nseg) {
+  if (p->kg_segment == C) return PAT_OK;
+  kg_free(p);
+  const size_t N = (size_t)p->N;
+  cudaError_t e = cudaMalloc(&p->kg_ckpt, sizeof(float) * N * 2 * nseg);
+  if (e == cudaSuccess) e = cudaMalloc(&p->kg_seg, sizeof(float) * N * C);
+  if (e == cudaSuccess) e = cudaMalloc(&p->kg_work, sizeof(float) * N * 3);
+  if (e == cudaSuccess) e = cudaMalloc(&p->kg_acc, sizeof(double) * N);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    kg_free(p);
+    return cuda_fail(e, "cudaMalloc(gradient checkpoints)");
+  }
+  p->kg_segment = C;
+  return PAT_OK;
+}
+
+pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float* g, int C, cudaStream_t st) {
+  const long long N = p->N;
+  const int nt = p->nt;
+  if (nt < 2) {
+    PAT_TRY_CUDA(fill_launch(g, N, 0.f, st));
+    return PAT_OK;
+  }
+  if (C <= 0) C = (int)std::ceil(std::sqrt((double)nt));
+  if (C > nt - 1) C = nt - 1;
+  const int nseg = (nt - 2) / C + 1;  // segments of n = 0 .. nt-2
+  PAT_TRY(kg_alloc(p, C, nseg));
+  const bool two_d = p->dim == 2;
+  float* W0 = p->kg_work;
+  float* W1 = p->kg_work + N;
+  float* W2 = p->kg_work + 2 * N;
+  auto ck = [&](int k, int f) { return p->kg_ckpt + ((size_t)k * 2 + f) * N; };
+  auto seg = [&](int j) { return p->kg_seg + (size_t)j * N; };
+  auto copy = [&](float* d, const float* s) {
+    return cudaMemcpyAsync(d, s, sizeof(float) * N, cudaMemcpyDeviceToDevice, st);
+  };
+  StepArgs a = step_args(p);
+  a.y = nullptr;
+
+  // ---- forward run keeping the restart state at n = 0, C, 2C, ...
+  if (two_d) {  // increment form: state (P^n, D^n)
+    a.dbuf = W2;
+    const float* cur = x;
+    for (int n = 0; n < nt - 1; ++n) {
+      if (n % C == 0) {
+        PAT_TRY_CUDA(copy(ck(n / C, 0), cur));
+        if (n > 0) PAT_TRY_CUDA(copy(ck(n / C, 1), W2));
+      }
+      a.cur = cur;
+      a.next = (n % 2) ? W1 : W0;
+      a.d_zero = (n == 0);
+      a.c_lap = (n == 0) ? 0.5f : 1.f;
+      PAT_TRY_CUDA(step_launch(p, false, a, st));
+      cur = a.next;
+    }
+  } else {  // three-level form: state (P^n, P^{n-1})
+    const float* prev = nullptr;
+    const float* cur = x;
+    float* bufs[3] = {W0, W1, W2};
+    for (int n = 0; n < nt - 1; ++n) {
+      if (n % C == 0) {
+        PAT_TRY_CUDA(copy(ck(n / C, 0), cur));
+        if (n > 0) PAT_TRY_CUDA(copy(ck(n / C, 1), prev));
+      }
+      a.cur = cur;
+      a.prev = prev;
+      a.next = bufs[n % 3];
+      a.c_cur = (n == 0) ? 1.f : 2.f;
+      a.c_prev = (n == 0) ? 0.f : 1.f;
+      a.c_lap = (n == 0) ? 0.5f : 1.f;
+      PAT_TRY_CUDA(step_launch(p, false, a, st));
+      prev = cur;
+      cur = a.next;
+    }
+  }
+
+  // ---- segment k holds P^n for n in [kC, min(kC + C, nt - 1))
+  int loaded = -1;
+  auto load_segment = [&](int k) -> pat_status {
+    const int n0 = k * C, n1 = std::min(n0 + C, nt - 1);
+    StepArgs b = step_args(p);
+    b.y = nullptr;
+    PAT_TRY_CUDA(copy(seg(0), ck(k, 0)));
+    if (two_d) {
+      if (n0 > 0) PAT_TRY_CUDA(copy(W2, ck(k, 1)));
+      b.dbuf = W2;
+      for (int n = n0; n < n1 - 1; ++n) {
+        b.cur = seg(n - n0);
+        b.next = seg(n + 1 - n0);
+        b.d_zero = (n == 0);
+        b.c_lap = (n == 0) ? 0.5f : 1.f;
+        PAT_TRY_CUDA(step_launch(p, false, b, st));
+      }
+    } else {
+      if (n0 > 0) PAT_TRY_CUDA(copy(W0, ck(k, 1)));
+      for (int n = n0; n < n1 - 1; ++n) {
+        b.cur = seg(n - n0);
+        b.prev = (n == 0) ? nullptr : (n == n0 ? W0 : seg(n - 1 - n0));
+        b.next = seg(n + 1 - n0);
+        b.c_cur = (n == 0) ? 1.f : 2.f;
+        b.c_prev = (n == 0) ? 0.f : 1.f;
+        b.c_lap = (n == 0) ? 0.5f : 1.f;
+        PAT_TRY_CUDA(step_launch(p, false, b, st));
+      }
+    }
+    loaded = k;
+    return PAT_OK;
+  };
+  // gradient term of the adjoint state Q^m: Q^m .* L P^{m-1}, halved for m = 1
+  auto accumulate = [&](int m, const float* Q, const float* Qlo) -> pat_status {
+    const int n = m - 1;
+    if (n / C != loaded) PAT_TRY(load_segment(n / C));
+    PAT_TRY_CUDA(grad_acc_launch(p->R, p->kg_acc, Q, Qlo, seg(n - loaded * C), n == 0 ? 0.5f : 1.f, a, p->dim, st));
+    return PAT_OK;
+  };
+  PAT_TRY_CUDA(dfill_launch(p->kg_acc, N, st));
+
+  // ---- adjoint run with the residual r, accumulating the gradient
+  auto inject = [&](float* Q, int t) {
+    return inject_launch(Q, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, r, nt, t, 1.f, st);
+  };
+  StepArgs c = step_args(p);
+  c.y = nullptr;
+  if (two_d) {
+    float* G = p->d_wv[2];
+    auto Qbuf = [&](int m) { return p->d_wv[(nt - m) % 2]; };
+    auto Qlo = [&](int m) { return p->d_wv[3 + (nt - m) % 2]; };
+    PAT_TRY_CUDA(fill_launch(G, N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(p->d_wv[5], N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(Qbuf(nt), N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(Qlo(nt), N, 0.f, st));
+    c.dbuf = G;
+    c.dbuf_lo = p->d_wv[5];
+    for (int m = nt - 1; m >= 1; --m) {
+      PAT_TRY_CUDA(inject(G, m));
+      c.cur = Qbuf(m + 1);
+      c.cur_lo = Qlo(m + 1);
+      c.next = Qbuf(m);
+      c.next_lo = Qlo(m);
+      c.d_zero = 0;
+      c.final_step = 0;
+      c.c_lap = 1.f;
+      PAT_TRY_CUDA(step_launch(p, true, c, st));
+      PAT_TRY(accumulate(m, Qbuf(m), Qlo(m)));
+    }
+  } else {
+    auto Qbuf = [&](int m) { return p->d_wv[(nt - 1 - m) % 3]; };
+    PAT_TRY_CUDA(fill_launch(Qbuf(nt - 1), N, 0.f, st));
+    PAT_TRY_CUDA(inject(Qbuf(nt - 1), nt - 1));
+    PAT_TRY(accumulate(nt - 1, Qbuf(nt - 1), nullptr));
+    for (int m = nt - 2; m >= 1; --m) {
+      c.cur = Qbuf(m + 1);
+      c.prev = (m + 2 <= nt - 1) ? Qbuf(m + 2) : nullptr;
+      c.next = Qbuf(m);
+      c.c_cur = 2.f;
+      c.c_prev = 1.f;
+      c.c_lap = 1.f;
+      PAT_TRY_CUDA(step_launch(p, true, c, st));
+      PAT_TRY_CUDA(inject(Qbuf(m), m));
+      PAT_TRY(accumulate(m, Qbuf(m), nullptr));
+    }
+  }
+  PAT_TRY_CUDA(d2f_launch(g, p->kg_acc, N, st));
+  return PAT_OK;
+}
+
 // --------------------------------------------------------------------- CG
 static pat_status apply_normal(pat_plan* p, double s, const float* v, float* out, cudaStream_t st) {
   // out = E_s* K* K E_s v   (alpha v is added by the fused dot kernel)
@@ -561,6 +743,24 @@ pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* 
     if (s != PAT_OK && first == PAT_OK) first = s;
   }
   return first;
+}
+
+pat_status pat_grad_kappa(pat_plan* plan, const float* x, const float* r, float* g, int segment, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!x || !g || (!r && plan->ns > 0) || segment < 0) {
+    set_error("x, r and g must not be NULL and segment >= 0");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float *dx, *dr;
+  float* dg;
+  bool hx, hr, hg;
+  PAT_TRY(in_arr(plan, 0, x, plan->N, &dx, &hx, st));
+  PAT_TRY(in_arr(plan, 1, r, ny, &dr, &hr, st));
+  PAT_TRY(out_arr(plan, 2, g, plan->N, &dg, &hg));
+  PAT_TRY(kappa_grad_device(plan, dx, dr, dg, segment, st));
+  return out_back(g, dg, plan->N, hg, st);
 }
 
 pat_status pat_plan_profile(pat_plan* plan, int enable) {

@@ -506,6 +506,10 @@ void pat_plan_destroy(pat_plan* plan) {
   for (int i = 0; i < 4; ++i)
     if (plan->d_stage[i]) cudaFree(plan->d_stage[i]);
   for (cudaEvent_t e : plan->prof_ev) cudaEventDestroy(e);
+  cudaFree(plan->kg_ckpt);
+  cudaFree(plan->kg_seg);
+  cudaFree(plan->kg_work);
+  cudaFree(plan->kg_acc);
   delete plan;
 }
 

@@ -71,6 +71,13 @@ struct pat_plan {
   float* d_stage[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t stage_bytes[4] = {0, 0, 0, 0};
 
+  // ---- medium-gradient workspace (allocated by the first pat_grad_kappa call)
+  int kg_segment = 0;           // checkpoint interval the buffers were sized for
+  float* kg_ckpt = nullptr;     // per checkpoint: two fields (P and D, or P and P^{n-1})
+  float* kg_seg = nullptr;      // one segment of recomputed fields
+  float* kg_work = nullptr;     // forward-pass fields (3 x N)
+  double* kg_acc = nullptr;     // FP64 gradient accumulator
+
   // ---- measurement hooks
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
@@ -89,4 +96,5 @@ pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_
 pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream_t st);
 pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int iters, const float* u0, float* u,
                         float* x, double* log, cudaStream_t st);
+pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float* g, int segment, cudaStream_t st);
 }  // namespace pat

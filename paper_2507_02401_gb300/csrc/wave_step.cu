@@ -340,4 +340,78 @@ cudaError_t copy_launch(float* d, const float* s, long long n, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------- medium gradient
+// gacc[i] += coef * (Q[i] + Qlo[i]) * (L P)[i]: one term of
+//   d<r, K x>/d kappa = sum_{n>=1} Q^{n+1} .* L P^n + 1/2 Q^1 .* L P^0,
+// the explicit kappa-dependence of P^{n+1} = 2P^n - P^{n-1} + kappa .* L P^n
+// weighted by the adjoint state.  L P is the zero-sum difference form with
+// zero outside the grid; the sum over steps is kept in FP64.
+namespace {
+template <int R>
+__global__ void grad_acc_kernel(double* __restrict__ gacc, const float* __restrict__ Q, const float* __restrict__ Qlo,
+                                const float* __restrict__ P, float coef, int nx, int ny, int nz, int dim,
+                                const StepArgs a) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const int y = (int)((i / nx) % ny);
+    const int z = (int)(i / ((long long)nx * ny));
+    const float c = P[i];
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+      const float xp = (x + m < nx) ? P[i + m] : 0.f;
+      const float xm = (x - m >= 0) ? P[i - m] : 0.f;
+      const float yp = (y + m < ny) ? P[i + (long long)m * nx] : 0.f;
+      const float ym = (y - m >= 0) ? P[i - (long long)m * nx] : 0.f;
+      float t = ((xp - c) + (xm - c)) + ((yp - c) + (ym - c));
+      if (dim == 3) {
+        const long long pl = (long long)nx * ny;
+        const float zp = (z + m < nz) ? P[i + m * pl] : 0.f;
+        const float zm = (z - m >= 0) ? P[i - m * pl] : 0.f;
+        t += (zp - c) + (zm - c);
+      }
+      acc = fmaf(a.w[m], t, acc);
+    }
+    const double q = (double)Q[i] + (Qlo ? (double)Qlo[i] : 0.0);
+    gacc[i] += (double)coef * q * (double)acc;
+  }
+}
+
+__global__ void d2f_kernel(float* __restrict__ out, const double* __restrict__ in, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+__global__ void dfill_kernel(double* __restrict__ p, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0.0;
+}
+}  // namespace
+
+cudaError_t grad_acc_launch(int R, double* gacc, const float* Q, const float* Qlo, const float* P, float coef,
+                            const StepArgs& a, int dim, cudaStream_t st) {
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  const int blocks = grid_for(N);
+  switch (R) {
+    case 1: grad_acc_kernel<1><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
+    case 3: grad_acc_kernel<3><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
+    case 5: grad_acc_kernel<5><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
+    case 7: grad_acc_kernel<7><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t d2f_launch(float* out, const double* in, long long n, cudaStream_t st) {
+  d2f_kernel<<<grid_for(n), 256, 0, st>>>(out, in, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dfill_launch(double* p, long long n, cudaStream_t st) {
+  dfill_kernel<<<grid_for(n), 256, 0, st>>>(p, n);
+  return cudaGetLastError();
+}
+
 }  // namespace pat

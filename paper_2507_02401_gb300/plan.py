@@ -101,6 +101,14 @@ class Plan:
         _lib.pat_EsT(self.handle, s, x, u, self._stream(stream))
         return u
 
+    def grad_kappa(self, x, r, segment=0, stream=None):
+        """d<r, K x>/d kappa per cell (float32 tensor of `shape`)."""
+        x = self._f32(x)
+        r = self._f32(r)
+        g = torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        _lib.pat_grad_kappa(self.handle, x, r, g, segment, self._stream(stream))
+        return g
+
     def solve(self, y, alpha, s, iters, u0=None, want_log=False, stream=None):
         """CG solve; returns (u, x, log) as device tensors (log: (iters, 3) float64 or None)."""
         y = self._f32(y)
