@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 PAT library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -125,6 +126,15 @@ int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
 cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, int nsplit, int nt, float* y,
                                     cudaStream_t st);
+
+// wave3d_tma.cu: constant-medium 3D step with TMA plane pipelines
+bool tma3d_supported(int nx, int R, bool varc);
+// `cur` (80 x (16+2R) x 1 boxes) and `prev` (64 x 16 x 1) descriptors of an nx x ny x nz float field
+cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev);
+int tma3d_zchunk(int nx, int ny, int nz);
+long long tma3d_threads(int nx, int ny, int nz, int zchunk);  // threads of one launch (fused sampling)
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+                              int* status, long long timeout_ns, cudaStream_t st);
 
 // wave_step.cu
 cudaError_t step2d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);

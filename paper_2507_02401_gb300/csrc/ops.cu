@@ -61,6 +61,24 @@ static StepArgs step_args(pat_plan* p) {
   return a;
 }
 
+// Tensor-map descriptors of a field, encoded on first use and kept per address.
+static const pat_plan::TmaDesc* tma_desc(pat_plan* p, const float* base) {
+  for (auto& d : p->tma_desc)
+    if (d.base == base) return &d;
+  pat_plan::TmaDesc d;
+  d.base = base;
+  if (tma3d_encode(base, p->n[0], p->n[1], p->n[2], p->R, &d.cur, &d.prev) != cudaSuccess) return nullptr;
+  if (p->tma_desc.size() >= 16) p->tma_desc.erase(p->tma_desc.begin());
+  p->tma_desc.push_back(d);
+  return &p->tma_desc.back();
+}
+
+// The TMA kernel takes 16-byte aligned fields (descriptor bases, float4 stores).
+static bool tma_ready(pat_plan*, const StepArgs& a) {
+  auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+  return al(a.cur) && al(a.prev) && al(a.next);
+}
+
 static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t st) {
   // sample separately when the step grid has fewer threads than sensors
   float* y = a.y;
@@ -69,6 +87,20 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;
     e = step2d_launch(p->R, adj, a, st);
+  } else if (p->tma3d && tma_ready(p, a)) {
+    const long long nthr = tma3d_threads(p->n[0], p->n[1], p->n[2], p->tma3d_zchunk);
+    if (y && a.ns > nthr) a.y = nullptr;
+    CUtensorMap mc, mp;
+    const pat_plan::TmaDesc* dc = tma_desc(p, a.cur);
+    if (!dc) return cudaErrorInvalidValue;
+    mc = dc->cur;
+    mp = dc->prev;  // unused when there is no previous field
+    if (a.prev) {
+      const pat_plan::TmaDesc* dp = tma_desc(p, a.prev);
+      if (!dp) return cudaErrorInvalidValue;
+      mp = dp->prev;
+    }
+    e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_zchunk, p->d_status, p->timeout_ns, st);
   } else {
     const long long nthr =
         (long long)((p->n[0] + 31) / 32) * ((p->n[1] + 15) / 16) * ((p->n[2] + 31) / 32) * 128;
@@ -797,7 +829,7 @@ pat_status pat_plan_check(pat_plan* plan, void* stream) {
   PAT_TRY_CUDA(cudaMemcpy(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   const int zero = 0;
   PAT_TRY_CUDA(cudaMemcpy(plan->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice));
-  if (status == PAT_ERR_TIMEOUT) set_error("a bounded wait in the persistent wave kernel ran out");
+  if (status == PAT_ERR_TIMEOUT) set_error("a bounded wait in a wave kernel ran out");
   if (status == PAT_ERR_BREAKDOWN) set_error("CG breakdown: p.q <= 0 or a non-finite step length");
   return (pat_status)status;
 }

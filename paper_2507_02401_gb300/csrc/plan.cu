@@ -466,6 +466,17 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   p->path = p->persist_ok ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
   const char* env = getenv("PAT_WAVE_PATH");
   if (env && strcmp(env, "step") == 0) p->path = PAT_PATH_STEP;
+
+  // 3D constant media: TMA plane pipelines when the driver can encode the descriptors
+  p->tma3d = false;
+  const char* env3 = getenv("PAT_STEP3D");
+  if (p->dim == 3 && tma3d_supported(p->n[0], p->R, p->varc) && !(env3 && strcmp(env3, "plain") == 0)) {
+    CUtensorMap mc, mp;
+    if (tma3d_encode(p->d_wv[0], p->n[0], p->n[1], p->n[2], p->R, &mc, &mp) == cudaSuccess) {
+      p->tma3d = true;
+      p->tma3d_zchunk = tma3d_zchunk(p->n[0], p->n[1], p->n[2]);
+    }
+  }
   PAT_TRY_CUDA(cudaStreamSynchronize(st));
   return PAT_OK;
 }

@@ -53,6 +53,13 @@ struct pat_plan {
   long long timeout_ns = 2000000000LL;
   int poll_ns = 0;  // exchange polling back-off
   float* d_wv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per-step engine fields
+  bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
+  int tma3d_zchunk = 0;
+  struct TmaDesc {
+    const float* base;
+    CUtensorMap cur, prev;
+  };
+  std::vector<TmaDesc> tma_desc;  // descriptors by field address (small, most recent last)
 
   // ---- wavelet scratch
   float* d_dwt_a = nullptr;  // approximation ping-pong (2 x N/2^dim)

@@ -1,0 +1,261 @@
+// 3D wave step with TMA-fed plane pipelines (constant medium, the HBM-bound
+// volumes): one launch per time step of the three-level recurrence
+//
+//   next = c_cur cur - c_prev prev + c_lap (kappa_hi + kappa_lo) L cur
+//
+// (paper Sec. 2, Eq. wave_equation; forward P^{n+1} = 2P^n - P^{n-1} +
+// kappa L P^n and, because kappa is constant, the adjoint
+// Q^n = 2Q^{n+1} - Q^{n+2} + kappa L Q^{n+1} have the same form).
+//
+// A CTA owns a 64 x 16 column of cells and marches through a chunk of z
+// planes.  One thread issues TMA loads of each plane of `cur` as an
+// (64+16) x (16+2R) box (x/y halo included, zero outside the grid) into a
+// ring of shared-memory slots, PD planes ahead of the plane being computed,
+// plus the own 64 x 16 tile of `prev`; completion is tracked by one mbarrier
+// per slot.  Each thread owns 2 rows x 4 columns: x/y neighbours come from the
+// centre plane's slot, z neighbours from a register queue of 2R+1 planes.
+// Compulsory DRAM traffic per point-update: cur and prev read once, next
+// written once (12 B); halo re-reads are served by L2.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "stencil.cuh"
+#include "tma.cuh"
+
+namespace pat {
+namespace {
+
+constexpr int TX = 64, TY = 16, THREADS = (TX / 4) * (TY / 2);  // 128
+constexpr int XH = 8;            // box columns left of the tile (>= R, 16-byte aligned)
+constexpr int BW = TX + 2 * XH;  // box width, 80 floats
+constexpr int PD = 2;            // prefetch distance in planes
+
+template <int R>
+struct G3 {
+  static constexpr int BH = TY + 2 * R;
+  static constexpr int PLANE = BW * BH;  // floats per cur slot (multiple of 32: 128-byte aligned slots)
+  static constexpr int NS = R + 1 + PD;  // cur slots: centre plane .. queue plane + PD
+  static constexpr int PREV = TX * TY;   // floats per prev slot
+  static constexpr int NSP = PD + 1;
+  static constexpr size_t SMEM = sizeof(float) * ((size_t)NS * PLANE + (size_t)NSP * PREV) + 8 * (NS + NSP);
+};
+
+__device__ __forceinline__ void fused_sample3(const StepArgs& a, long long gtid) {
+  if (a.y == nullptr || gtid >= a.ns) return;
+  const int s = (int)gtid;
+  float v = 0.f;
+  for (int k = 0; k < a.corners; ++k) v = fmaf(a.sens_w[s * a.corners + k], a.cur[a.sens_cell[s * a.corners + k]], v);
+  a.y[(long long)s * a.nt + a.t_sample] = v;
+}
+
+template <int R>
+__global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mcur,
+                                                             const __grid_constant__ CUtensorMap mprev, int zchunk,
+                                                             int* status, long long timeout_ns) {
+  using G = G3<R>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  float* pring = ring + G::NS * G::PLANE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(pring + G::NSP * G::PREV);
+  uint64_t* pbars = bars + G::NS;
+
+  const int t = threadIdx.x;
+  const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  fused_sample3(a, bid * THREADS + t);
+
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long plane = (long long)nx * ny;
+  const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * 2;
+  const int gx0 = blockIdx.x * TX, gy0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, nz);
+  const int nloc = z1 - z0;         // planes computed
+  const int ncur = nloc + R;        // cur planes j = 0 .. ncur-1 (z = z0 + j) go through the ring
+  const bool has_prev = a.prev != nullptr;
+  const float ck = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
+
+  if (t == 0) {
+    for (int s = 0; s < G::NS + G::NSP; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int issued = 0;  // cur planes issued (thread 0)
+  auto issue_cur = [&](int j) {
+    issued = j + 1;
+    const int s = j % G::NS;
+    mbar_expect_tx(&bars[s], G::PLANE * 4);
+    tma_load_3d(ring + s * G::PLANE, &mcur, gx0 - XH, gy0 - R, z0 + j, &bars[s]);
+  };
+  int issued_prev = 0;
+  auto issue_prev = [&](int j) {
+    issued_prev = j + 1;
+    const int s = j % G::NSP;
+    mbar_expect_tx(&pbars[s], G::PREV * 4);
+    tma_load_3d(pring + s * G::PREV, &mprev, gx0, gy0, z0 + j, &pbars[s]);
+  };
+  if (t == 0) {
+    for (int j = 0; j < min(R + PD, ncur); ++j) issue_cur(j);
+    if (has_prev)
+      for (int j = 0; j < min(PD, nloc); ++j) issue_prev(j);
+  }
+
+  // register queue of the own cells: q[i] = plane z - R + i
+  float4 q[2 * R + 1][2];
+#pragma unroll
+  for (int i = 0; i < R; ++i)  // planes z0-R .. z0-1 straight from global memory
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int z = z0 - R + i, gy = gy0 + r0 + rr, gx = gx0 + c0;
+      q[i][rr] = (z >= 0 && gy < ny && gx < nx)
+                     ? __ldg(reinterpret_cast<const float4*>(a.cur + z * plane + (long long)gy * nx + gx))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {  // planes z0 .. z0+R-1 from the ring
+    ok = ok && (i >= ncur || mbar_wait(&bars[i % G::NS], (i / G::NS) & 1, timeout_ns));
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+      q[R + i][rr] = *reinterpret_cast<const float4*>(ring + (i % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
+  }
+
+  bool ok_all = true;
+  for (int i = 0; i < nloc; ++i) {
+    if (t == 0) {
+      fence_proxy_async_shared();  // the slots refilled below were last read through the generic proxy
+      if (i + R + PD < ncur) issue_cur(i + R + PD);
+      if (has_prev && i + PD < nloc) issue_prev(i + PD);
+    }
+    const int jq = i + R;  // queue plane
+    bool good = ok && mbar_wait(&bars[jq % G::NS], (jq / G::NS) & 1, timeout_ns);
+    if (has_prev) good = good && mbar_wait(&pbars[i % G::NSP], (i / G::NSP) & 1, timeout_ns);
+    if (__syncthreads_or(!good)) {
+      if (t == 0) atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
+      ok_all = false;
+      break;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+      q[2 * R][rr] = *reinterpret_cast<const float4*>(ring + (jq % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
+
+    const float* cen = ring + (i % G::NS) * G::PLANE;
+    float L[2][4];
+    lap_2x4<R, false, false>(cen, BW, r0 + R, XH + c0, a.w, L);
+    const int z = z0 + i;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      float out[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float c = f4get(q[R][rr], j);
+        const float c2 = c + c;
+        float acc = L[rr][j];
+#pragma unroll
+        for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], (f4get(q[R + m][rr], j) + f4get(q[R - m][rr], j)) - c2, acc);
+        float v = a.c_cur * c;
+        if (has_prev) v -= a.c_prev * f4get(*reinterpret_cast<const float4*>(pring + (i % G::NSP) * G::PREV +
+                                                                             (r0 + rr) * TX + c0),
+                                            j);
+        out[j] = v + fmaf(ck, acc, ckl * acc);
+      }
+      const int gy = gy0 + r0 + rr, gx = gx0 + c0;
+      if (gy < ny && gx < nx)
+        *reinterpret_cast<float4*>(a.next + z * plane + (long long)gy * nx + gx) =
+            make_float4(out[0], out[1], out[2], out[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+      q[k][0] = q[k + 1][0];
+      q[k][1] = q[k + 1][1];
+    }
+    __syncthreads();  // the centre slot is refilled by the next iteration's TMA
+  }
+  // after a timed-out wait: give the copies still in flight (the last one of
+  // each slot) a bounded chance to land before the CTA's shared memory goes away
+  if (t == 0 && !ok_all) {
+    for (int j = max(0, issued - G::NS); j < issued; ++j) mbar_wait(&bars[j % G::NS], (j / G::NS) & 1, timeout_ns);
+    for (int j = max(0, issued_prev - G::NSP); j < issued_prev; ++j)
+      mbar_wait(&pbars[j % G::NSP], (j / G::NSP) & 1, timeout_ns);
+  }
+}
+
+template <int R>
+cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int zchunk, int* status,
+                     long long timeout_ns, cudaStream_t st) {
+  const size_t smem = G3<R>::SMEM;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
+  step3d_tma_kernel<R><<<grid, THREADS, smem, st>>>(a, mc, mp, zchunk, status, timeout_ns);
+  return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+}  // namespace
+
+bool tma3d_supported(int nx, int R, bool varc) { return !varc && nx % 4 == 0 && (R == 1 || R == 3 || R == 5 || R == 7); }
+
+// Descriptors of a 3D field: `cur` boxes (80 x (16+2R) x 1) and `prev` boxes (64 x 16 x 1).
+cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t box_c[3] = {(cuuint32_t)BW, (cuuint32_t)(TY + 2 * R), 1};
+  const cuuint32_t box_p[3] = {(cuuint32_t)TX, (cuuint32_t)TY, 1};
+  CUresult r1 = fn(cur, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box_c, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = fn(prev, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box_p, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int tma3d_zchunk(int nx, int ny, int nz) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long cols = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  int zc = 16;  // aim at >= 3 CTAs per SM, chunks of at least 16 planes
+  while (zc < nz && cols * ((nz + zc * 2 - 1) / (zc * 2)) >= 3LL * sms) zc *= 2;
+  return zc;
+}
+
+long long tma3d_threads(int nx, int ny, int nz, int zchunk) {
+  return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk) * THREADS;
+}
+
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+                              int* status, long long timeout_ns, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_r<1>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 3: return launch_r<3>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 5: return launch_r<5>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 7: return launch_r<7>(a, cur, prev, zchunk, status, timeout_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pat
