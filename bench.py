@@ -13,8 +13,16 @@ power iteration before timing).  Metric: reconstruction iterations per second
 With N > 1 (torchrun) every rank solves its own independently seeded
 instance (weak scaling, no data-path collective).
 
+--workload tree3d times the 3D 256^3 order-4 workload instead (4096
+sensors on a sphere, 800 time samples, 3D db4 with 4 levels, 30 CG
+iterations per step).
+
+--sweep prints one line per grid of the per-step engines' HBM sweep
+(2D 2048^2 .. 16384^2 x orders {2, 8}, 3D 256^3 and 512^3 order 4).
+
 --impl reference runs the FP64 CPU oracle (the reference arm of this
-build): each step is one oracle CG iteration of the same workload.
+build): each step is one oracle CG iteration of the same workload (for the
+volume, one K + K* pair at 40 steps scaled linearly to the full 800).
 """
 import argparse
 import csv
@@ -36,9 +44,28 @@ if ROOT not in sys.path:
 METRIC = "reconstruction iterations/sec (K+K* pairs)"
 UNIT = "iterations/s"
 WORKLOAD = "vessels"
-WORKLOAD_DESC = ("2D 512x512, c in [1400,1600] m/s (Gaussian-filtered noise), order-8 staggered FDTD, 1500 steps, "
+# per workload: description, timed kernel, committed ncu summary and the sources it was taken on
+WORKLOADS = {
+    "vessels": {
+        "desc": ("2D 512x512, c in [1400,1600] m/s (Gaussian-filtered noise), order-8 staggered FDTD, 1500 steps, "
                  "512 sensors on a circle, p0 = 4 blobs + 6 Bezier vessels, 2% noise, db4 5 levels, "
-                 "s in {1,2} x alpha in {1e-3,1e-2}, 100 CG iterations, FP32 fields + FP64 CG scalars")
+                 "s in {1,2} x alpha in {1e-3,1e-2}, 100 CG iterations, FP32 fields + FP64 CG scalars"),
+        "kernel": "wave2d_persist_kernel<R=7,varc>",
+        "profile": "wave2d_persist_512_o8.txt",
+        "sources": ("wave2d_persist.cu", "stencil.cuh"),
+        "oracle_nt": None,
+    },
+    "tree3d": {
+        "desc": ("3D 256^3, c = 1500 m/s, order-4 staggered FDTD, 800 steps, 4096 sensors on a Fibonacci sphere, "
+                 "p0 = vessel tree + 5 blobs, 1% noise, 3D db4 4 levels, s = 1, alpha = 1e-2, 30 CG iterations, "
+                 "FP32 fields + FP64 CG scalars"),
+        "kernel": "step3d_tma_kernel<R=3>",
+        "profile": "step3d_tma_256_o4.txt",
+        "sources": ("wave3d_tma.cu", "stencil.cuh", "tma.cuh"),
+        "oracle_nt": 40,  # oracle samples: one K + K* pair at 40 steps, scaled linearly to 800
+    },
+}
+WORKLOAD_DESC = WORKLOADS[WORKLOAD]["desc"]
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -51,15 +78,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the persistent wave kernel from the committed
-    ncu summary, or None if absent or taken on a different kernel source."""
+def kernel_traffic(workload):
+    """DRAM bytes per launch of the workload's dominant kernel from the
+    committed ncu summary, or None if absent or taken on a different source."""
+    spec = WORKLOADS[workload]
     src = hashlib.sha256()
-    for f in ("wave2d_persist.cu", "stencil.cuh"):
+    for f in spec["sources"]:
         with open(os.path.join(ROOT, "paper_2507_02401_gb300", "csrc", f), "rb") as fh:
             src.update(fh.read())
     digest = src.hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "wave2d_persist_512_o8.txt")
+    path = os.path.join(ROOT, "profiles", spec["profile"])
     if not os.path.exists(path):
         return None, digest
     vals = {}
@@ -163,10 +191,28 @@ def gpu_index(local):
     return local
 
 
-def cpu_baseline(w, iters_sample):
-    """The FP64 oracle, as it stands, on the host cores: `iters_sample` CG
-    iterations (one K, one K*, E_s, E_s* each) of the same workload."""
+def oracle_pairs_per_s(w, nt_sample):
+    """One oracle K + K* pair of the workload at nt_sample steps, scaled
+    linearly in nt to pairs per second at the full nt; (value, seconds)."""
     import oracle
+    wave = oracle.Wave(w.shape, w.h, w.dt, nt_sample, w.order, w.c_array(), w.sensors)
+    t0 = time.perf_counter()
+    wave.adjoint(wave.forward(w.x_true))
+    dt = time.perf_counter() - t0
+    return (nt_sample - 1) / ((w.nt - 1) * dt), dt
+
+
+def cpu_baseline(w, iters_sample, workload):
+    """The FP64 oracle, as it stands, on the host cores: `iters_sample` CG
+    iterations (one K, one K*, E_s, E_s* each) of the same workload, or for
+    the volume one K + K* pair at a reduced step count scaled to the full one."""
+    import oracle
+    nt_s = WORKLOADS[workload]["oracle_nt"]
+    if nt_s:
+        value, dt = oracle_pairs_per_s(w, nt_s)
+        return {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                "sample": f"oracle FP64 K + K* of the full {'x'.join(map(str, w.shape))} grid at {nt_s} of "
+                          f"{w.nt} steps ({dt:.1f} s), scaled linearly in steps; E_s/CG vector work not counted"}
     wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
     wav = oracle.Wavelet(w.shape, w.family, w.levels)
     rng = np.random.default_rng(0)
@@ -177,39 +223,53 @@ def cpu_baseline(w, iters_sample):
     # a solve of k iterations costs 1 + 2k wave solves; count iterations as (2k+1)/2 pairs
     pairs = (2 * iters_sample + 1) / 2.0
     return {"value": pairs / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"oracle FP64 CG, {iters_sample} iterations (+ right-hand side) of the full 512x512 workload; "
-                      f"{dt:.1f} s"}
+            "sample": f"oracle FP64 CG, {iters_sample} iterations (+ right-hand side) of the full "
+                      f"{'x'.join(map(str, w.shape))} workload; {dt:.1f} s"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, timed per step on one CG iteration."""
+    """Reference arm: the FP64 CPU oracle; each step is one CG iteration of
+    the workload (the volume: one K + K* pair at a reduced step count, scaled
+    linearly to the full one)."""
     import synth
     import oracle
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = synth.workload(WORKLOAD)
-    wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
-    wav = oracle.Wavelet(w.shape, w.family, w.levels)
-    H = oracle.normal_op(wave, wav, 1.0, 1e-3)
-    rng = np.random.default_rng(0)
-    p = rng.standard_normal(w.N)
-    for _ in range(args.warmup):
-        H(p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        q = H(p)
-        a = float(p @ p) / float(p @ q)
-        p = p - a * q  # the CG vector work of one iteration is negligible beside H
-    dt = time.perf_counter() - t0
+    w = synth.workload(args.workload)
+    nt_s = WORKLOADS[args.workload]["oracle_nt"]
+    if nt_s:
+        for _ in range(args.warmup):
+            oracle_pairs_per_s(w, nt_s)
+        t_full = 0.0
+        for _ in range(args.steps):
+            v, _ = oracle_pairs_per_s(w, nt_s)
+            t_full += 1.0 / v
+        dt = t_full
+        step_desc = f"one oracle K + K* pair at {nt_s} of {w.nt} steps, scaled linearly to the full step count"
+    else:
+        wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
+        wav = oracle.Wavelet(w.shape, w.family, w.levels)
+        H = oracle.normal_op(wave, wav, 1.0, 1e-3)
+        rng = np.random.default_rng(0)
+        p = rng.standard_normal(w.N)
+        for _ in range(args.warmup):
+            H(p)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            q = H(p)
+            a = float(p @ p) / float(p @ q)
+            p = p - a * q  # the CG vector work of one iteration is negligible beside H
+        dt = time.perf_counter() - t0
+        step_desc = "one oracle CG iteration (K + K* + E_s + E_s*)"
     value = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "step": "one oracle CG iteration (K + K* + E_s + E_s*)"},
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "step": step_desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle CG iterations after {args.warmup} warm-up"},
+                             "sample": f"{args.steps} timed steps ({step_desc}) after {args.warmup} warm-up"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -238,7 +298,8 @@ def run_ours(args):
         print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
         return 1
     rank, world, local = dist_setup(True)
-    w = synth.workload(WORKLOAD, seed=1001 + rank)
+    spec = WORKLOADS[args.workload]
+    w = synth.workload(args.workload, seed=(1001 if args.workload == "vessels" else 1004) + rank)
     if args.iters:
         w.iters = args.iters
     c = w.c if np.ndim(w.c) == 0 else w.c_array()
@@ -250,7 +311,7 @@ def run_ours(args):
     y = torch.as_tensor(y_np, device="cuda")
     combos = []
     for s in w.s:
-        lam = lambda_max(plan, s)
+        lam = lambda_max(plan, s, iters=args.power_iters)
         for a in w.alpha:
             combos.append((s, a * lam))
     u = torch.empty(plan.N, device="cuda")
@@ -305,25 +366,32 @@ def run_ours(args):
     iters_total = world * args.steps * w.iters
     value = iters_total / (t_ms / 1e3)
     bytes_per_pt = 16 if plan_varc(w) else 12
-    per_launch_bytes = bytes_per_pt * w.N * (w.nt - 1)
-    achieved = per_launch_bytes * wave_calls / (wave_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
+    # the persistent engine runs a whole K or K* per launch, the step engines one time step
+    steps_per_launch = (w.nt - 1) if plan.path == 1 else 1
+    launches = wave_calls * (w.nt - 1) // steps_per_launch
+    per_launch_bytes = bytes_per_pt * w.N * steps_per_launch
+    launch_ms = wave_ms / max(launches, 1)
+    achieved = per_launch_bytes / (launch_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
     peak, peak_kind = peaks()
-    traffic, digest = kernel_traffic()
+    traffic, digest = kernel_traffic(args.workload)
     engine = {1: "persistent", 2: "step"}.get(plan.path, "?")
     gpts = world * args.steps * (2 * w.iters + 1) * (w.nt - 1) * w.N / (t_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "engine": engine, "iters_per_step": w.iters,
+        "config": {"workload": spec["desc"], "engine": engine, "iters_per_step": w.iters,
                    "l2": "256 MiB buffer written before every step (inside the timed region)",
                    "parallelism": f"replicas x{world} (independent instances per rank)"},
         "gpoint_updates_per_s": gpts,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"wave2d_persist_kernel<R=7,varc> ({engine} engine)",
+                     "kernel": f"{spec['kernel']} ({engine} engine)",
                      "algorithmic_bytes_per_point_update": bytes_per_pt,
-                     "launch_ms": wave_ms / max(wave_calls, 1), "launches_timed": wave_calls,
+                     "launch_ms": launch_ms, "launches_timed": launches,
+                     "launch": "one K or K* application" if steps_per_launch > 1 else
+                               "one time step (averaged over whole K / K* applications, sampling and "
+                               "injection launches included)",
                      "source_sha256_16": digest},
         "e2e": {"value": iters_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_np.nbytes),
                 "d2h_bytes_per_step": int(w.N * 4)},
@@ -331,13 +399,65 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_iters)
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_iters, args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     plan.close()
+    return 0
+
+
+def run_sweep(args):
+    """Per-step wave engines on HBM-sized grids: one JSON line per case with
+    the time per step of K and K* (CUDA events, whole applications of 200
+    steps, fields larger than L2) and the algorithmic GB/s against the HBM
+    peak (12 B per point-update for a constant medium, 16 B for a varying one)."""
+    import torch
+    from paper_2507_02401_gb300 import Plan
+    peak, peak_kind = peaks()
+    cases = [((n, n), o, False) for n in (2048, 4096, 8192, 16384) for o in (2, 8)]
+    cases += [((4096, 4096), 8, True), ((256, 256, 256), 4, False), ((512, 512, 512), 4, False)]
+    nt = 201
+    if args.only:
+        cases = [cs for cs in cases if "x".join(map(str, cs[0])) == args.only]
+    for shape, order, varc in cases:
+        h = 1e-4
+        rng = np.random.default_rng(0)
+        c = 1400.0 + 200.0 * rng.random(shape).astype(np.float32) if varc else 1500.0
+        dt = 0.3 * h / 1600.0
+        sens = np.stack([rng.uniform(0.1, 0.9, 64) * (n - 1) * h for n in shape[::-1]], axis=1)
+        plan = Plan(shape, h, dt, nt, order, c, sens, 1, 0)
+        x = torch.randn(shape, device="cuda")
+        y = torch.empty((64, nt), device="cuda")
+        xa = torch.empty(shape, device="cuda")
+        res = {}
+        for name, fn in (("K", lambda: plan.forward(x, out=y)), ("Kt", lambda: plan.adjoint(y, out=xa))):
+            for _ in range(args.warmup):
+                fn()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(args.steps):
+                fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            res[name] = ev0.elapsed_time(ev1) * 1e3 / args.steps / (nt - 1)
+        assert plan.check() == 0
+        N = int(np.prod(shape))
+        bpp = 16 if varc else 12
+        line = {"sweep": "x".join(map(str, shape)), "order": order, "medium": "varying" if varc else "constant",
+                "engine": {1: "persistent", 2: "step"}.get(plan.path, "?"), "steps": nt - 1,
+                "algorithmic_bytes_per_point_update": bpp, "peak_gbs": peak, "peak_kind": peak_kind}
+        for name in ("K", "Kt"):
+            us = res[name]
+            gbs = N * bpp / us / 1e3
+            line[name] = {"us_per_step": round(us, 2), "gpoint_updates_per_s": round(N / us / 1e3, 1),
+                          "algorithmic_gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        print(json.dumps(line), flush=True)
+        plan.close()
+        del x, y, xa
+        torch.cuda.empty_cache()
     return 0
 
 
@@ -351,13 +471,20 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     ap.add_argument("--iters", type=int, default=0, help="override CG iterations per step")
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle CG iterations in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--power-iters", type=int, default=20, help="power iterations for lambda_max")
+    ap.add_argument("--only", default="", help="with --sweep: run only the grid named like 256x256x256")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time the per-step wave engines on 2D 2048^2..16384^2 (orders 2, 8) and 3D grids instead")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 
