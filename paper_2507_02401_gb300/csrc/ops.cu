@@ -67,23 +67,42 @@ static const pat_plan::TmaDesc* tma_desc(pat_plan* p, const float* base) {
     if (d.base == base) return &d;
   pat_plan::TmaDesc d;
   d.base = base;
-  if (tma3d_encode(base, p->n[0], p->n[1], p->n[2], p->R, &d.cur, &d.prev) != cudaSuccess) return nullptr;
+  const cudaError_t e = p->dim == 3 ? tma3d_encode(base, p->n[0], p->n[1], p->n[2], p->R, &d.halo, &d.own)
+                                     : tma2d_encode(base, p->n[0], p->n[1], p->R, &d.halo, &d.own);
+  if (e != cudaSuccess) return nullptr;
   if (p->tma_desc.size() >= 16) p->tma_desc.erase(p->tma_desc.begin());
   p->tma_desc.push_back(d);
   return &p->tma_desc.back();
 }
 
-// The TMA kernel takes 16-byte aligned fields (descriptor bases, float4 stores).
-static bool tma_ready(pat_plan*, const StepArgs& a) {
+// The TMA kernels take 16-byte aligned fields (descriptor bases, float4 stores).
+static bool tma_ready(pat_plan* p, const StepArgs& a) {
   auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
-  return al(a.cur) && al(a.prev) && al(a.next);
+  return al(a.cur) && al(a.prev) && al(a.next) && (p->dim == 3 || al(a.dbuf));
 }
 
 static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t st) {
   // sample separately when the step grid has fewer threads than sensors
   float* y = a.y;
   cudaError_t e;
-  if (p->dim == 2) {
+  if (p->dim == 2 && p->tma2d && !(adj && p->varc) && tma_ready(p, a)) {
+    // forward, and the constant-medium adjoint (same recurrence): TMA tile pipelines
+    const bool varc = p->varc && !adj;
+    const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, varc);
+    if (y && a.ns > nthr) a.y = nullptr;
+    const pat_plan::TmaDesc* dp = tma_desc(p, a.cur);
+    if (!dp) return cudaErrorInvalidValue;
+    const CUtensorMap mp = dp->halo;
+    CUtensorMap md = dp->own;  // unused when D starts at zero
+    if (!a.d_zero) {
+      const pat_plan::TmaDesc* dd = tma_desc(p, a.dbuf);
+      if (!dd) return cudaErrorInvalidValue;
+      md = dd->own;
+    }
+    StepArgs b = a;
+    if (!varc) b.kappa = b.kappa_lo = nullptr;
+    e = step2d_tma_launch(p->R, varc, b, mp, md, p->d_status, p->timeout_ns, st);
+  } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;
     e = step2d_launch(p->R, adj, a, st);
@@ -93,12 +112,12 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     CUtensorMap mc, mp;
     const pat_plan::TmaDesc* dc = tma_desc(p, a.cur);
     if (!dc) return cudaErrorInvalidValue;
-    mc = dc->cur;
-    mp = dc->prev;  // unused when there is no previous field
+    mc = dc->halo;
+    mp = dc->own;  // unused when there is no previous field
     if (a.prev) {
       const pat_plan::TmaDesc* dp = tma_desc(p, a.prev);
       if (!dp) return cudaErrorInvalidValue;
-      mp = dp->prev;
+      mp = dp->own;
     }
     e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_zchunk, p->d_status, p->timeout_ns, st);
   } else {

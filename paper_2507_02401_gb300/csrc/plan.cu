@@ -467,6 +467,14 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   const char* env = getenv("PAT_WAVE_PATH");
   if (env && strcmp(env, "step") == 0) p->path = PAT_PATH_STEP;
 
+  // 2D per-step engine: TMA tile pipelines when the driver can encode the descriptors
+  p->tma2d = false;
+  const char* env2 = getenv("PAT_STEP2D");
+  if (p->dim == 2 && tma2d_supported(p->n[0], p->R) && !(env2 && strcmp(env2, "plain") == 0)) {
+    CUtensorMap mh, mo;
+    if (tma2d_encode(p->d_wv[0], p->n[0], p->n[1], p->R, &mh, &mo) == cudaSuccess) p->tma2d = true;
+  }
+
   // 3D constant media: TMA plane pipelines when the driver can encode the descriptors
   p->tma3d = false;
   const char* env3 = getenv("PAT_STEP3D");

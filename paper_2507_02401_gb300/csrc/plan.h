@@ -55,9 +55,10 @@ struct pat_plan {
   float* d_wv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per-step engine fields
   bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
   int tma3d_zchunk = 0;
+  bool tma2d = false;  // 2D steps through the TMA tile-pipeline kernel (where it applies)
   struct TmaDesc {
     const float* base;
-    CUtensorMap cur, prev;
+    CUtensorMap halo, own;  // stencil-input boxes with halo, own-tile boxes
   };
   std::vector<TmaDesc> tma_desc;  // descriptors by field address (small, most recent last)
 

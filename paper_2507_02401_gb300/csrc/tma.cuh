@@ -4,11 +4,18 @@
 #include <cuda.h>  // CUtensorMap (type only; descriptors are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include <cstdint>
 
 #include "stencil.cuh"
 
 namespace pat {
+
+void* tma_encoder_raw();
+inline PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tma_encoder_raw());
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 

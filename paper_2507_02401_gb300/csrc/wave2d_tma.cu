@@ -1,0 +1,254 @@
+// 2D wave step with TMA-fed tile pipelines: one launch per time step of the
+// increment form (paper Sec. 2, Eq. wave_equation, eliminated to p only)
+//
+//   D^{n+1} = D^n + c_lap (kappa_hi + kappa_lo) L P^n,   P^{n+1} = P^n + D^{n+1}
+//
+// For a constant medium the adjoint recurrence has the same form,
+// G^m = G^{m+1} + S^T r_m + kappa L Q^{m+1}, Q^m = Q^{m+1} + G^m, and runs
+// through the same kernel (the injection S^T r_m is added to G beforehand;
+// the final step writes x = G + c_lap kappa L Q^1).
+//
+// Persistent CTAs walk 64 x 64 tiles; one thread issues TMA loads of the next
+// tile's P box (80 x (64+2R), halo included, zero outside the grid) and D
+// tile into the second of two shared-memory stages while the CTA computes the
+// current one.  Each thread owns 4 columns x 8 consecutive rows: y neighbours
+// come from a sliding register window of 2R+1 rows, x neighbours from the
+// shared-memory row.  Compulsory DRAM traffic per point-update: P and D read,
+// P^{n+1} and D^{n+1} written (16 B), plus kappa hi/lo (8 B) for a varying
+// medium.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "stencil.cuh"
+#include "tma.cuh"
+
+namespace pat {
+namespace {
+
+constexpr int TX = 64, TY = 64, RUN = 8;
+constexpr int TCOLS = TX / 4, TROWS = TY / RUN, THREADS = TCOLS * TROWS;  // 16 x 8 = 128
+constexpr int XH = 8;            // box columns left of the tile (>= R, 16-byte aligned)
+constexpr int BW = TX + 2 * XH;  // P box width, 80 floats
+
+template <int R>
+struct G2 {
+  static constexpr int BH = TY + 2 * R;
+  static constexpr int PBOX = BW * BH;  // floats (multiple of 32: 128-byte aligned)
+  static constexpr int DBOX = TX * TY;
+  static constexpr int STAGE = PBOX + DBOX;
+  static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
+};
+
+__device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid) {
+  if (a.y == nullptr || gtid >= a.ns) return;
+  const int s = (int)gtid;
+  float v = 0.f;
+  for (int k = 0; k < a.corners; ++k) v = fmaf(a.sens_w[s * a.corners + k], a.cur[a.sens_cell[s * a.corners + k]], v);
+  a.y[(long long)s * a.nt + a.t_sample] = v;
+}
+
+template <int R, bool VARC>
+__global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
+                                                             const __grid_constant__ CUtensorMap md, int* status,
+                                                             long long timeout_ns) {
+  using G = G2<R>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage0 = reinterpret_cast<float*>(smem_raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
+
+  const int t = threadIdx.x;
+  fused_sample2(a, (long long)blockIdx.x * THREADS + t);
+
+  const int nx = a.nx, ny = a.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int ntiles = tiles_x * ((ny + TY - 1) / TY);
+  const int c0 = (t % TCOLS) * 4, r0 = (t / TCOLS) * RUN;
+  const bool load_d = !a.d_zero;
+  const unsigned stage_bytes = (unsigned)(G::PBOX + (load_d ? G::DBOX : 0)) * 4u;
+
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int tile, int s) {
+    float* st = stage0 + s * G::STAGE;
+    const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
+    mbar_expect_tx(&bars[s], stage_bytes);
+    tma_load_2d(st, &mp, gx0 - XH, gy0 - R, &bars[s]);
+    if (load_d) tma_load_2d(st + G::PBOX, &md, gx0, gy0, &bars[s]);
+  };
+  int first = blockIdx.x;
+  if (t == 0 && first < ntiles) issue(first, 0);
+
+  const float ckh = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
+  int k = 0;
+  bool ok = true;
+  int issued = (first < ntiles) ? 1 : 0;
+  for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
+    const int s = k & 1;
+    if (t == 0) {
+      fence_proxy_async_shared();  // the other stage was last read through the generic proxy
+      const int nxt = tile + gridDim.x;
+      if (nxt < ntiles) {
+        issue(nxt, s ^ 1);
+        ++issued;
+      }
+    }
+    const bool good = mbar_wait(&bars[s], (k >> 1) & 1, timeout_ns);
+    if (__syncthreads_or(!good)) {
+      if (t == 0) atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
+      ok = false;
+      break;
+    }
+    const float* P = stage0 + s * G::STAGE;
+    const float* Dt = P + G::PBOX;
+    const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
+    const int gx = gx0 + c0;
+
+    // sliding window over this thread's 4 columns: win[i] = box row (row - R + i)
+    float4 win[2 * R + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(P + (r0 + i) * BW + XH + c0);
+#pragma unroll
+    for (int rr = 0; rr < RUN; ++rr) {
+      win[2 * R] = *reinterpret_cast<const float4*>(P + (r0 + rr + 2 * R) * BW + XH + c0);
+      const int brow = r0 + rr + R;
+      float f[20];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(P + brow * BW + c0 + 4 * q);
+        f[4 * q + 0] = v.x;
+        f[4 * q + 1] = v.y;
+        f[4 * q + 2] = v.z;
+        f[4 * q + 3] = v.w;
+      }
+      const int gy = gy0 + r0 + rr;
+      const long long gi = (long long)gy * nx + gx;
+      const bool in = gy < ny && gx < nx;
+      float4 kh4 = make_float4(a.kappa0, a.kappa0, a.kappa0, a.kappa0);
+      float4 kl4 = make_float4(a.kappa0_lo, a.kappa0_lo, a.kappa0_lo, a.kappa0_lo);
+      if (VARC && in) {
+        kh4 = __ldg(reinterpret_cast<const float4*>(a.kappa + gi));
+        kl4 = __ldg(reinterpret_cast<const float4*>(a.kappa_lo + gi));
+      }
+      const float4 d4 = load_d ? *reinterpret_cast<const float4*>(Dt + (r0 + rr) * TX + c0)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      float dn[4], pn[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float c = f[8 + j];
+        const float c2 = c + c;
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 1; m <= R; ++m)
+          acc = fmaf(a.w[m], pair_term<true>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<true>(f[8 + j + m], f[8 + j - m], c, c2), acc);
+        float inc;
+        if (VARC)
+          inc = fmaf(a.c_lap * f4get(kh4, j), acc, (a.c_lap * f4get(kl4, j)) * acc);
+        else
+          inc = fmaf(ckh, acc, ckl * acc);
+        dn[j] = f4get(d4, j) + inc;
+        pn[j] = a.final_step ? dn[j] : c + dn[j];
+      }
+      if (in) {
+        *reinterpret_cast<float4*>(a.next + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        if (!a.final_step) *reinterpret_cast<float4*>(a.dbuf + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
+    }
+    __syncthreads();  // this stage is refilled by the next iteration's TMA
+  }
+  // after a timed-out wait: give the copies in flight a bounded chance to land
+  if (t == 0 && !ok)
+    for (int j = max(0, issued - 2); j < issued; ++j) mbar_wait(&bars[j & 1], (j >> 1) & 1, timeout_ns);
+}
+
+template <int R, bool VARC>
+cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mp, const CUtensorMap& md, int nctas, int* status,
+                     long long timeout_ns, cudaStream_t st) {
+  const size_t smem = G2<R>::SMEM;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(step2d_tma_kernel<R, VARC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  step2d_tma_kernel<R, VARC><<<nctas, THREADS, smem, st>>>(a, mp, md, status, timeout_ns);
+  return cudaGetLastError();
+}
+
+template <bool VARC>
+cudaError_t launch_v(int R, const StepArgs& a, const CUtensorMap& mp, const CUtensorMap& md, int nctas, int* status,
+                     long long timeout_ns, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_r<1, VARC>(a, mp, md, nctas, status, timeout_ns, st);
+    case 3: return launch_r<3, VARC>(a, mp, md, nctas, status, timeout_ns, st);
+    case 5: return launch_r<5, VARC>(a, mp, md, nctas, status, timeout_ns, st);
+    case 7: return launch_r<7, VARC>(a, mp, md, nctas, status, timeout_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool tma2d_supported(int nx, int R) { return nx % 4 == 0 && (R == 1 || R == 3 || R == 5 || R == 7); }
+
+// Descriptors of a 2D field: P boxes (80 x (64+2R)) and own-tile boxes (64 x 64).
+cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* halo, CUtensorMap* own) {
+  auto fn = tma_encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint32_t box_h[2] = {(cuuint32_t)BW, (cuuint32_t)(TY + 2 * R)};
+  const cuuint32_t box_o[2] = {(cuuint32_t)TX, (cuuint32_t)TY};
+  CUresult r1 = fn(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box_h, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = fn(own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box_o, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Persistent grid: as many CTAs as fit (2 per SM at order 8), at most one per tile.
+int tma2d_ctas(int nx, int ny, int R, bool varc) {
+  static int cached[2][8] = {{0}};
+  int& c = cached[varc ? 1 : 0][R];
+  if (!c) {
+    int dev = 0, sms = 148, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = R == 1 ? G2<1>::SMEM : R == 3 ? G2<3>::SMEM : R == 5 ? G2<5>::SMEM : G2<7>::SMEM;
+    const void* fn = R == 1   ? (varc ? (const void*)step2d_tma_kernel<1, true> : (const void*)step2d_tma_kernel<1, false>)
+                     : R == 3 ? (varc ? (const void*)step2d_tma_kernel<3, true> : (const void*)step2d_tma_kernel<3, false>)
+                     : R == 5 ? (varc ? (const void*)step2d_tma_kernel<5, true> : (const void*)step2d_tma_kernel<5, false>)
+                              : (varc ? (const void*)step2d_tma_kernel<7, true> : (const void*)step2d_tma_kernel<7, false>);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, THREADS, smem) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    c = per * sms;
+  }
+  const int ntiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  return ntiles < c ? ntiles : c;
+}
+
+long long tma2d_threads(int nx, int ny, int R, bool varc) { return (long long)tma2d_ctas(nx, ny, R, varc) * THREADS; }
+
+cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& d,
+                              int* status, long long timeout_ns, cudaStream_t st) {
+  const int nctas = tma2d_ctas(a.nx, a.ny, R, varc);
+  return varc ? launch_v<true>(R, a, p, d, nctas, status, timeout_ns, st)
+              : launch_v<false>(R, a, p, d, nctas, status, timeout_ns, st);
+}
+
+}  // namespace pat

@@ -197,28 +197,31 @@ cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap
   return cudaGetLastError();
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+}  // namespace
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link);
+// nullptr when the driver does not provide it.
+void* tma_encoder_raw() {
+  static void* fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+      fn = p;
     else
       cudaGetLastError();
   });
   return fn;
 }
 
-}  // namespace
 
 bool tma3d_supported(int nx, int R, bool varc) { return !varc && nx % 4 == 0 && (R == 1 || R == 3 || R == 5 || R == 7); }
 
 // Descriptors of a 3D field: `cur` boxes (80 x (16+2R) x 1) and `prev` boxes (64 x 16 x 1).
 cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev) {
-  auto fn = encode_fn();
+  auto fn = tma_encoder();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
