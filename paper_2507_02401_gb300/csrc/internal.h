@@ -141,8 +141,8 @@ bool tma2d_supported(int nx, int R);
 // P boxes (80 x (64+2R)) and own-tile boxes (64 x 64) of an nx x ny float field
 cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* halo, CUtensorMap* own);
 long long tma2d_threads(int nx, int ny, int R, bool varc);  // threads of one launch (fused sampling)
-cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& d,
-                              int* status, long long timeout_ns, cudaStream_t st);
+cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, int* status,
+                              long long timeout_ns, cudaStream_t st);
 
 // wave_step.cu
 cudaError_t step2d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);

@@ -92,16 +92,9 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     if (y && a.ns > nthr) a.y = nullptr;
     const pat_plan::TmaDesc* dp = tma_desc(p, a.cur);
     if (!dp) return cudaErrorInvalidValue;
-    const CUtensorMap mp = dp->halo;
-    CUtensorMap md = dp->own;  // unused when D starts at zero
-    if (!a.d_zero) {
-      const pat_plan::TmaDesc* dd = tma_desc(p, a.dbuf);
-      if (!dd) return cudaErrorInvalidValue;
-      md = dd->own;
-    }
     StepArgs b = a;
     if (!varc) b.kappa = b.kappa_lo = nullptr;
-    e = step2d_tma_launch(p->R, varc, b, mp, md, p->d_status, p->timeout_ns, st);
+    e = step2d_tma_launch(p->R, varc, b, dp->halo, p->d_status, p->timeout_ns, st);
   } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;

@@ -80,6 +80,15 @@ __device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, 
   }
 }
 
+// 16-byte load of data read once per launch (streamed: no L1 allocation)
+__device__ __forceinline__ float4 ld_stream4(const float* p) {
+  float4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
 // Knuth's TwoSum: returns s = fl(a + b) and sets e so that s + e == a + b
 // exactly (no reassociation: the library is built without fast-math).
 __device__ __forceinline__ float two_sum(float a, float b, float& e) {

@@ -8,14 +8,15 @@
 // through the same kernel (the injection S^T r_m is added to G beforehand;
 // the final step writes x = G + c_lap kappa L Q^1).
 //
-// Persistent CTAs walk 64 x 64 tiles; one thread issues TMA loads of the next
-// tile's P box (80 x (64+2R), halo included, zero outside the grid) and D
-// tile into the second of two shared-memory stages while the CTA computes the
-// current one.  Each thread owns 4 columns x 8 consecutive rows: y neighbours
-// come from a sliding register window of 2R+1 rows, x neighbours from the
-// shared-memory row.  Compulsory DRAM traffic per point-update: P and D read,
-// P^{n+1} and D^{n+1} written (16 B), plus kappa hi/lo (8 B) for a varying
-// medium.
+// Persistent CTAs walk 64 x 64 tiles; one thread issues the TMA load of the
+// next tile's P box (80 x (64+2R), halo included, zero outside the grid) into
+// the second of two shared-memory stages while the CTA computes the current
+// one.  Each thread owns 4 columns x 8 consecutive rows: y neighbours come
+// from a sliding register window of 2R+1 rows, x neighbours from the
+// shared-memory row; its own D (and kappa) cells are loaded straight into
+// registers (coalesced 16-byte loads issued before the wait for the P box).
+// Compulsory DRAM traffic per point-update: P and D read, P^{n+1} and D^{n+1}
+// written (16 B), plus kappa hi/lo (8 B) for a varying medium.
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -36,8 +37,7 @@ template <int R>
 struct G2 {
   static constexpr int BH = TY + 2 * R;
   static constexpr int PBOX = BW * BH;  // floats (multiple of 32: 128-byte aligned)
-  static constexpr int DBOX = TX * TY;
-  static constexpr int STAGE = PBOX + DBOX;
+  static constexpr int STAGE = PBOX;
   static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
 };
 
@@ -51,8 +51,7 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
 
 template <int R, bool VARC>
 __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
-                                                             const __grid_constant__ CUtensorMap md, int* status,
-                                                             long long timeout_ns) {
+                                                             int* status, long long timeout_ns) {
   using G = G2<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
@@ -66,7 +65,7 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
   const int ntiles = tiles_x * ((ny + TY - 1) / TY);
   const int c0 = (t % TCOLS) * 4, r0 = (t / TCOLS) * RUN;
   const bool load_d = !a.d_zero;
-  const unsigned stage_bytes = (unsigned)(G::PBOX + (load_d ? G::DBOX : 0)) * 4u;
+  const unsigned stage_bytes = (unsigned)G::PBOX * 4u;
 
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -80,7 +79,6 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
     const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
     mbar_expect_tx(&bars[s], stage_bytes);
     tma_load_2d(st, &mp, gx0 - XH, gy0 - R, &bars[s]);
-    if (load_d) tma_load_2d(st + G::PBOX, &md, gx0, gy0, &bars[s]);
   };
   int first = blockIdx.x;
   if (t == 0 && first < ntiles) issue(first, 0);
@@ -99,6 +97,24 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
         ++issued;
       }
     }
+    const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
+    const int gx = gx0 + c0;
+    // own-cell fields straight into registers, in flight while the P box lands
+    float4 d4[RUN], kh4[RUN], kl4[RUN];
+#pragma unroll
+    for (int rr = 0; rr < RUN; ++rr) {
+      const int gy = gy0 + r0 + rr;
+      const bool in = gy < ny && gx < nx;
+      const long long gi = (long long)gy * nx + gx;
+      d4[rr] = (load_d && in) ? ld_stream4(a.dbuf + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (VARC) {
+        kh4[rr] = in ? __ldg(reinterpret_cast<const float4*>(a.kappa + gi)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        kl4[rr] = in ? __ldg(reinterpret_cast<const float4*>(a.kappa_lo + gi)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        kh4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+        kl4[rr] = kh4[rr];
+      }
+    }
     const bool good = mbar_wait(&bars[s], (k >> 1) & 1, timeout_ns);
     if (__syncthreads_or(!good)) {
       if (t == 0) atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -106,9 +122,6 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       break;
     }
     const float* P = stage0 + s * G::STAGE;
-    const float* Dt = P + G::PBOX;
-    const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
-    const int gx = gx0 + c0;
 
     // sliding window over this thread's 4 columns: win[i] = box row (row - R + i)
     float4 win[2 * R + 1];
@@ -130,14 +143,6 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       const int gy = gy0 + r0 + rr;
       const long long gi = (long long)gy * nx + gx;
       const bool in = gy < ny && gx < nx;
-      float4 kh4 = make_float4(a.kappa0, a.kappa0, a.kappa0, a.kappa0);
-      float4 kl4 = make_float4(a.kappa0_lo, a.kappa0_lo, a.kappa0_lo, a.kappa0_lo);
-      if (VARC && in) {
-        kh4 = __ldg(reinterpret_cast<const float4*>(a.kappa + gi));
-        kl4 = __ldg(reinterpret_cast<const float4*>(a.kappa_lo + gi));
-      }
-      const float4 d4 = load_d ? *reinterpret_cast<const float4*>(Dt + (r0 + rr) * TX + c0)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
       float dn[4], pn[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -151,10 +156,10 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
         for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<true>(f[8 + j + m], f[8 + j - m], c, c2), acc);
         float inc;
         if (VARC)
-          inc = fmaf(a.c_lap * f4get(kh4, j), acc, (a.c_lap * f4get(kl4, j)) * acc);
+          inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
         else
           inc = fmaf(ckh, acc, ckl * acc);
-        dn[j] = f4get(d4, j) + inc;
+        dn[j] = f4get(d4[rr], j) + inc;
         pn[j] = a.final_step ? dn[j] : c + dn[j];
       }
       if (in) {
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
 }
 
 template <int R, bool VARC>
-cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mp, const CUtensorMap& md, int nctas, int* status,
+cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mp, int nctas, int* status,
                      long long timeout_ns, cudaStream_t st) {
   const size_t smem = G2<R>::SMEM;
   static std::once_flag once;
@@ -181,18 +186,18 @@ cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mp, const CUtensorMap
     attr_err = cudaFuncSetAttribute(step2d_tma_kernel<R, VARC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  step2d_tma_kernel<R, VARC><<<nctas, THREADS, smem, st>>>(a, mp, md, status, timeout_ns);
+  step2d_tma_kernel<R, VARC><<<nctas, THREADS, smem, st>>>(a, mp, status, timeout_ns);
   return cudaGetLastError();
 }
 
 template <bool VARC>
-cudaError_t launch_v(int R, const StepArgs& a, const CUtensorMap& mp, const CUtensorMap& md, int nctas, int* status,
+cudaError_t launch_v(int R, const StepArgs& a, const CUtensorMap& mp, int nctas, int* status,
                      long long timeout_ns, cudaStream_t st) {
   switch (R) {
-    case 1: return launch_r<1, VARC>(a, mp, md, nctas, status, timeout_ns, st);
-    case 3: return launch_r<3, VARC>(a, mp, md, nctas, status, timeout_ns, st);
-    case 5: return launch_r<5, VARC>(a, mp, md, nctas, status, timeout_ns, st);
-    case 7: return launch_r<7, VARC>(a, mp, md, nctas, status, timeout_ns, st);
+    case 1: return launch_r<1, VARC>(a, mp, nctas, status, timeout_ns, st);
+    case 3: return launch_r<3, VARC>(a, mp, nctas, status, timeout_ns, st);
+    case 5: return launch_r<5, VARC>(a, mp, nctas, status, timeout_ns, st);
+    case 7: return launch_r<7, VARC>(a, mp, nctas, status, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -201,7 +206,8 @@ cudaError_t launch_v(int R, const StepArgs& a, const CUtensorMap& mp, const CUte
 
 bool tma2d_supported(int nx, int R) { return nx % 4 == 0 && (R == 1 || R == 3 || R == 5 || R == 7); }
 
-// Descriptors of a 2D field: P boxes (80 x (64+2R)) and own-tile boxes (64 x 64).
+// Descriptors of a 2D field: P boxes (80 x (64+2R)) and own-tile boxes (64 x 64, kept for
+// kernels that stage own cells through shared memory).
 cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* halo, CUtensorMap* own) {
   auto fn = tma_encoder();
   if (!fn) return cudaErrorNotSupported;
@@ -244,11 +250,11 @@ int tma2d_ctas(int nx, int ny, int R, bool varc) {
 
 long long tma2d_threads(int nx, int ny, int R, bool varc) { return (long long)tma2d_ctas(nx, ny, R, varc) * THREADS; }
 
-cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& d,
-                              int* status, long long timeout_ns, cudaStream_t st) {
+cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, int* status,
+                              long long timeout_ns, cudaStream_t st) {
   const int nctas = tma2d_ctas(a.nx, a.ny, R, varc);
-  return varc ? launch_v<true>(R, a, p, d, nctas, status, timeout_ns, st)
-              : launch_v<false>(R, a, p, d, nctas, status, timeout_ns, st);
+  return varc ? launch_v<true>(R, a, p, nctas, status, timeout_ns, st)
+              : launch_v<false>(R, a, p, nctas, status, timeout_ns, st);
 }
 
 }  // namespace pat
