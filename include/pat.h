@@ -151,6 +151,10 @@ pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int
 /*
  * pat_solve_batched — B independent pat_solve problems (each with its own
  * plan, data, alpha and s; a common iteration count) advanced together.
+ * When every plan qualifies for a batch (see pat_batch_create) and ys / xs
+ * are device arrays, this is pat_batch_create + pat_batch_solve +
+ * pat_batch_destroy (tuning included); otherwise the instances are solved
+ * one after the other with pat_solve.
  *   plans, ys, xs   host arrays of B plan / device-array pointers (xs[i]
  *                   receives E_s u of instance i).
  *   alphas, ss      host arrays of B doubles.
@@ -159,6 +163,53 @@ pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int
  */
 pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* ys, const double* alphas,
                              const double* ss, int iters, float* const* xs, pat_status* per_inst, void* stream);
+
+/*
+ * Batched engine.  Not in the paper (it reconstructs one image); the paper's
+ * CG (Sec. 4) is run for many independent problems at once.
+ *
+ * pat_batch_create — group B plans into one batch.  Every plan must be 2D,
+ * with a constant speed of sound, the same stencil order and nx % 4 == 0, and
+ * appear once (the batch uses each plan's device buffers; the plans must
+ * outlive the batch and must not be used concurrently with it).  Grid size,
+ * time samples, sensors, wavelet, alpha and s may differ.  All instances'
+ * 64-column tiles form one table; each time step of K or K* is one launch
+ * over the tiles of the instances still running.  The tile height (64 or 32
+ * rows) is chosen by timing both on the first steps of a batched K (an
+ * autotuner; PAT_BATCH_TILE_Y=64|32 in the environment fixes it).
+ * Synchronises `stream`.  Errors: PAT_ERR_INVALID (NULL, duplicate or
+ * ineligible plan), PAT_ERR_CUDA, PAT_ERR_OOM.
+ */
+typedef struct pat_batch pat_batch;
+pat_status pat_batch_create(pat_plan* const* plans, int B, void* stream, pat_batch** out);
+void pat_batch_destroy(pat_batch* batch);
+
+/*
+ * pat_batch_forward / pat_batch_adjoint — K (or K*) of every instance:
+ * xs[i] (N_i floats) -> ys[i] (ns_i x nt_i floats), or back.  Device arrays;
+ * asynchronous on `stream`.
+ */
+pat_status pat_batch_forward(pat_batch* batch, const float* const* xs, float* const* ys, void* stream);
+pat_status pat_batch_adjoint(pat_batch* batch, const float* const* ys, float* const* xs, void* stream);
+
+/*
+ * pat_batch_solve — pat_solve (u0 = 0) for every instance with its own
+ * alphas[i] and ss[i] and a common `iters`.  One CG iteration of all
+ * instances (E_s, batched K and K*, E_s*, FP64 CG scalars) is captured once
+ * as a CUDA graph (re-captured when alphas or ss change) and replayed
+ * `iters` times.  ys, xs: host arrays of B device pointers.  per_inst: NULL
+ * or B statuses (breakdown per instance, timeout of the batched kernel).
+ * Synchronous.  Returns the first non-OK status.
+ */
+pat_status pat_batch_solve(pat_batch* batch, const float* const* ys, const double* alphas, const double* ss,
+                           int iters, float* const* xs, pat_status* per_inst, void* stream);
+
+/*
+ * pat_batch_info — tile height in use, CTAs per step launch, nodes of the
+ * captured CG-iteration graph (0 before the first solve) and the autotuner's
+ * times (ms) of the 64-row and 32-row tiles.  Any output may be NULL.
+ */
+pat_status pat_batch_info(pat_batch* batch, int* tile_rows, int* ctas, long long* graph_nodes, double* tune_ms);
 
 /*
  * pat_grad_kappa — g = d<r, K x>/d kappa per cell, kappa = (c dt / h)^2: the

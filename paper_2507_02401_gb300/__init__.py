@@ -8,4 +8,4 @@ streams only.
 """
 from . import _lib  # noqa: F401
 from ._lib import PatError, PAT_PATH_AUTO, PAT_PATH_PERSISTENT, PAT_PATH_STEP  # noqa: F401
-from .plan import Plan  # noqa: F401
+from .plan import Batch, Plan  # noqa: F401

@@ -44,6 +44,13 @@ SIGNATURES = [
                           c_void_p]),
     ("pat_solve_batched", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p]),
+    ("pat_batch_create", c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
+    ("pat_batch_destroy", None, [c_void_p]),
+    ("pat_batch_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("pat_batch_adjoint", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("pat_batch_solve", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("pat_batch_info", c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_longlong),
+                               ctypes.POINTER(c_double)]),
     ("pat_grad_kappa", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("pat_plan_check", c_int, [c_void_p, c_void_p]),
     ("pat_plan_set_path", c_int, [c_void_p, c_int]),
@@ -168,6 +175,47 @@ def pat_solve_batched(plans, ys, alphas, ss, iters, xs, stream=None):
     st = (c_int * B)()
     rc = load().pat_solve_batched(P, B, Y, A, S, int(iters), X, st, stream_handle(stream))
     return rc, [int(v) for v in st]
+
+
+def _ptrs(arrs):
+    return (c_void_p * len(arrs))(*[ptr(a) for a in arrs])
+
+
+def pat_batch_create(plans, stream=None):
+    B = len(plans)
+    out = c_void_p()
+    _check(load().pat_batch_create((c_void_p * B)(*plans), B, stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def pat_batch_destroy(batch):
+    load().pat_batch_destroy(batch)
+
+
+def pat_batch_forward(batch, xs, ys, stream=None):
+    return _check(load().pat_batch_forward(batch, _ptrs(xs), _ptrs(ys), stream_handle(stream)))
+
+
+def pat_batch_adjoint(batch, ys, xs, stream=None):
+    return _check(load().pat_batch_adjoint(batch, _ptrs(ys), _ptrs(xs), stream_handle(stream)))
+
+
+def pat_batch_solve(batch, ys, alphas, ss, iters, xs, stream=None):
+    """Returns (status, per-instance statuses); no exception for device-side statuses."""
+    B = len(ys)
+    A = (c_double * B)(*[float(a) for a in alphas])
+    S = (c_double * B)(*[float(s) for s in ss])
+    st = (c_int * B)()
+    rc = load().pat_batch_solve(batch, _ptrs(ys), A, S, int(iters), _ptrs(xs), st, stream_handle(stream))
+    if rc in (PAT_ERR_INVALID, PAT_ERR_CUDA, PAT_ERR_OOM):
+        _check(rc)
+    return rc, [int(v) for v in st]
+
+
+def pat_batch_info(batch):
+    rows, ctas, nodes, tune = c_int(), c_int(), c_longlong(), (c_double * 2)()
+    _check(load().pat_batch_info(batch, ctypes.byref(rows), ctypes.byref(ctas), ctypes.byref(nodes), tune))
+    return {"tile_rows": rows.value, "ctas": ctas.value, "graph_nodes": nodes.value, "tune_ms": [tune[0], tune[1]]}
 
 
 def pat_grad_kappa(plan, x, r, g, segment=0, stream=None):

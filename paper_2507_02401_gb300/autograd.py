@@ -8,6 +8,7 @@ for E_s / E_s*):
     PatKt   x = K* y        backward  gy = K gx
     PatEs   x = E_s u       backward  gu = E_s* gx
     PatEsT  u = E_s* x      backward  gx = E_s gu
+    PatBatchK  [K_i x_i]    backward  [K_i* gy_i]   (one batched launch sequence)
 
 Tensors are float32 on the plan's device; the calls run on the current CUDA
 stream.  `reconstruction_loss` composes them into the regularised objective
@@ -89,6 +90,30 @@ class PatEsT(torch.autograd.Function):
         gx = torch.empty(plan.shape, device=gu.device, dtype=torch.float32)
         _lib.pat_Es(plan.handle, ctx.s, _f32(gu), gx, _stream())
         return None, None, gx
+
+
+class PatBatchK(torch.autograd.Function):
+    """K of every instance of a Batch: forward runs the batched engine's K,
+    backward its K* (inputs and outputs are B tensors each)."""
+
+    @staticmethod
+    def forward(ctx, batch, *xs):
+        ctx.batch = batch
+        ys = [torch.empty((p.ns, p.nt), device=x.device, dtype=torch.float32) for p, x in zip(batch.plans, xs)]
+        _lib.pat_batch_forward(batch.handle, [_f32(x) for x in xs], ys, _stream())
+        return tuple(ys)
+
+    @staticmethod
+    def backward(ctx, *gys):
+        batch = ctx.batch
+        gys = [torch.zeros((p.ns, p.nt), device="cuda") if g is None else g for p, g in zip(batch.plans, gys)]
+        gxs = [torch.empty(p.shape, device=g.device, dtype=torch.float32) for p, g in zip(batch.plans, gys)]
+        _lib.pat_batch_adjoint(batch.handle, [_f32(g) for g in gys], gxs, _stream())
+        return (None,) + tuple(gxs)
+
+
+def batch_K(batch, xs):
+    return list(PatBatchK.apply(batch, *xs))
 
 
 def K(plan, x):

@@ -1,0 +1,71 @@
+// Batched 2D engine: many independent constant-medium problems advanced one
+// time step per launch over a common table of 64-column tiles.
+#pragma once
+
+#include <vector>
+
+#include "plan.h"
+
+namespace pat {
+
+// One instance as seen by the batched step kernel (device memory).
+struct BInst {
+  int nx, ny, nt, tiles_x;
+  int tile0;  // first entry of this instance in the tile table
+  int ns, corners;
+  float kappa0, kappa0_lo;
+  const float* img;  // forward input P^0 / adjoint output x (the plan's image buffer)
+  float* P[2];       // ping-pong fields: P^n (forward) or Q^m (adjoint)
+  float* D;          // increment D (forward) or G (adjoint), updated in place
+  float* y;          // sensor data: forward output, adjoint input (ns x nt)
+  const int* sens_cell;
+  const float* sens_w;
+  const int* samp_ptr;  // per local tile: range into samp (sensors whose base cell is in the tile)
+  const int* samp;
+  const int* inj_ptr;   // per local tile: range into inj (injected cells of the tile)
+  const InjCell* inj;   // .local holds the cell's linear index
+  const int* ent_sensor;
+  const float* ent_w;
+};
+
+struct BatchStepArgs {
+  const BInst* inst;
+  const int* tile_inst;       // tile -> instance
+  const CUtensorMap* maps;    // 3 per instance: P[0], P[1], img (halo boxes)
+  int t;                      // global step: forward n = t, adjoint m = nt - 1 - t
+  int adjoint;
+  int active;                 // tiles of the instances still running at step t (a prefix of the table)
+  float w[kMaxR + 1];
+  int* status;
+  long long timeout_ns;
+};
+
+// batch.cu: every plan 2D, constant medium, one stencil order, nx % 4 == 0, no plan twice
+bool batch_eligible(pat_plan* const* plans, int B);
+
+// batch_kernels.cu
+int batch_tile_y(int variant);  // tile height of a kernel variant (0: 64 rows, 1: 32 rows)
+size_t batch_smem(int R, int variant);
+int batch_max_ctas(int R, int variant);  // co-resident CTAs on this device
+cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st);
+cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map);
+
+}  // namespace pat
+
+struct pat_batch {
+  std::vector<pat_plan*> plans;  // borrowed, in the caller's order
+  std::vector<int> order;        // instance slots sorted by nt, longest first (slot -> caller index)
+  int B = 0, R = 1, variant = 0, nctas = 0, max_nt = 0, ntiles = 0;
+  std::vector<int> active;       // active[t]: tiles still running at global step t
+  pat::BInst* d_inst = nullptr;
+  int* d_tile_inst = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  int* d_status = nullptr;       // timeout of a bounded wait in the batched kernel
+  long long timeout_ns = 2000000000LL;
+  std::vector<void*> allocations;
+  cudaStream_t cap = nullptr;    // capture stream
+  cudaGraphExec_t graph = nullptr;  // one CG iteration of every instance
+  std::vector<double> graph_alpha, graph_s;
+  size_t graph_nodes = 0;
+  double tune_ms[2] = {0, 0};
+};

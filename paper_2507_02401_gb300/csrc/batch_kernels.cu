@@ -1,0 +1,241 @@
+// Batched 2D step kernel: one launch advances every running instance of a
+// batch by one time step of the increment form (paper Sec. 2, Eq.
+// wave_equation, eliminated to p only; constant medium, so the adjoint has
+// the same recurrence):
+//
+//   forward, n = t:          D <- D + c_lap kappa L P^n,   P^{n+1} = P^n + D,   y[., n] = S P^n
+//   adjoint, m = nt - 1 - t: G <- G + S^T r_m + kappa L Q^{m+1},  Q^m = Q^{m+1} + G
+//                            (m = 0: x = G + 1/2 kappa L Q^1)
+//
+// The tiles (64 columns x 64 or 32 rows) of all instances form one table,
+// instances ordered by their number of time samples (longest first), so the
+// tiles still running at global step t are a prefix of the table.  Persistent
+// CTAs walk that prefix with the tile pipeline of the single-instance 2D step
+// kernel: TMA halo boxes of P in two shared-memory stages, D in registers, a
+// sliding y window per thread.  Sampling and injection are fused per tile
+// (each tile samples the sensors whose base cell it holds and injects into
+// its own cells).
+#include <mutex>
+
+#include "batch.h"
+#include "stencil.cuh"
+#include "tma.cuh"
+
+namespace pat {
+namespace {
+
+constexpr int TX = 64, RUN = 8, XH = 8, BW = TX + 2 * XH;
+
+template <int R, int TY>
+struct GB {
+  static constexpr int THREADS = (TX / 4) * (TY / RUN);
+  static constexpr int PBOX = BW * (TY + 2 * R);  // floats (multiple of 32: 128-byte aligned stages)
+  static constexpr size_t SMEM = sizeof(float) * 2 * PBOX + 16;
+};
+
+template <int R, int TY>
+__global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const BatchStepArgs a) {
+  using G = GB<R, TY>;
+  constexpr int THREADS = G::THREADS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage0 = reinterpret_cast<float*>(smem_raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::PBOX);
+
+  const int t = threadIdx.x;
+  const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * RUN;
+  const int step = a.t;
+  const bool adj = a.adjoint != 0;
+
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // halo box of the field the tile's stencil reads at this step
+  auto issue = [&](int tile, int s) {
+    const int ii = a.tile_inst[tile];
+    const BInst& I = a.inst[ii];
+    const int lt = tile - I.tile0;
+    const int gx0 = (lt % I.tiles_x) * TX, gy0 = (lt / I.tiles_x) * TY;
+    const CUtensorMap* map = a.maps + 3 * ii + ((!adj && step == 0) ? 2 : (step & 1));
+    mbar_expect_tx(&bars[s], (unsigned)G::PBOX * 4u);
+    tma_load_2d(stage0 + s * G::PBOX, map, gx0 - XH, gy0 - R, &bars[s]);
+  };
+  if (t == 0 && (int)blockIdx.x < a.active) issue(blockIdx.x, 0);
+
+  int k = 0, issued = ((int)blockIdx.x < a.active) ? 1 : 0;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < a.active; tile += gridDim.x, ++k) {
+    const int s = k & 1;
+    if (t == 0) {
+      fence_proxy_async_shared();  // the other stage was last read through the generic proxy
+      const int nxt = tile + gridDim.x;
+      if (nxt < a.active) {
+        issue(nxt, s ^ 1);
+        ++issued;
+      }
+    }
+    const int ii = a.tile_inst[tile];
+    const BInst& I = a.inst[ii];
+    const int nx = I.nx, ny = I.ny, nt = I.nt;
+    const int lt = tile - I.tile0;
+    const int gx0 = (lt % I.tiles_x) * TX, gy0 = (lt / I.tiles_x) * TY;
+    const int gx = gx0 + c0;
+    const int n = adj ? nt - 1 - step : step;  // the instance's own time index
+    const float* cur = (!adj && step == 0) ? I.img : I.P[step & 1];
+    const bool final_step = adj && n == 0;
+    const bool compute = adj || n < nt - 1;  // the forward's last index only samples
+    float* out = final_step ? const_cast<float*>(I.img) : I.P[(step + 1) & 1];
+
+    if (!adj) {  // y[s, n] = sum_k w_k P^n[cell_k] for the sensors based in this tile
+      for (int e = I.samp_ptr[lt] + t; e < I.samp_ptr[lt + 1]; e += THREADS) {
+        const int sn = I.samp[e];
+        float v = 0.f;
+        for (int q = 0; q < I.corners; ++q)
+          v = fmaf(I.sens_w[sn * I.corners + q], cur[I.sens_cell[sn * I.corners + q]], v);
+        I.y[(long long)sn * nt + n] = v;
+      }
+    } else {  // G += S^T r_m on the tile's own cells
+      for (int e = I.inj_ptr[lt] + t; e < I.inj_ptr[lt + 1]; e += THREADS) {
+        const InjCell c = I.inj[e];
+        float v = 0.f;
+        for (int q = c.beg; q < c.end; ++q) v = fmaf(I.ent_w[q], I.y[(long long)I.ent_sensor[q] * nt + n], v);
+        I.D[c.local] += v;
+      }
+      __syncthreads();  // the injected cells are read below by other threads of the CTA
+    }
+
+    const bool load_d = !(!adj && n == 0);
+    float4 d4[RUN];
+#pragma unroll
+    for (int rr = 0; rr < RUN; ++rr) {
+      const int gy = gy0 + r0 + rr;
+      const bool in = compute && load_d && gy < ny && gx < nx;
+      d4[rr] = in ? ld_stream4(I.D + (long long)gy * nx + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool good = mbar_wait(&bars[s], (k >> 1) & 1, a.timeout_ns);
+    if (__syncthreads_or(!good)) {
+      if (t == 0) atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
+      ok = false;
+      break;
+    }
+    if (compute) {
+      const float* P = stage0 + s * G::PBOX;
+      const float c_lap = (n == 0 || final_step) ? 0.5f : 1.f;
+      const float ckh = c_lap * I.kappa0, ckl = c_lap * I.kappa0_lo;
+      float4 win[2 * R + 1];
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(P + (r0 + i) * BW + XH + c0);
+#pragma unroll
+      for (int rr = 0; rr < RUN; ++rr) {
+        win[2 * R] = *reinterpret_cast<const float4*>(P + (r0 + rr + 2 * R) * BW + XH + c0);
+        const int brow = r0 + rr + R;
+        float f[20];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(P + brow * BW + c0 + 4 * q);
+          f[4 * q + 0] = v.x;
+          f[4 * q + 1] = v.y;
+          f[4 * q + 2] = v.z;
+          f[4 * q + 3] = v.w;
+        }
+        float dn[4], pn[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float c = f[8 + j];
+          const float c2 = c + c;
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 1; m <= R; ++m)
+            acc = fmaf(a.w[m], pair_term<true>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
+#pragma unroll
+          for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<true>(f[8 + j + m], f[8 + j - m], c, c2), acc);
+          dn[j] = f4get(d4[rr], j) + fmaf(ckh, acc, ckl * acc);
+          pn[j] = final_step ? dn[j] : c + dn[j];
+        }
+        const int gy = gy0 + r0 + rr;
+        if (gy < ny && gx < nx) {
+          const long long gi = (long long)gy * nx + gx;
+          *reinterpret_cast<float4*>(out + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+          if (!final_step) *reinterpret_cast<float4*>(I.D + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
+      }
+    }
+    __syncthreads();  // this stage is refilled by the next iteration's TMA
+  }
+  // after a timed-out wait: give the copies in flight a bounded chance to land
+  if (t == 0 && !ok)
+    for (int j = max(0, issued - 2); j < issued; ++j) mbar_wait(&bars[j & 1], (j >> 1) & 1, a.timeout_ns);
+}
+
+template <int R, int TY>
+const void* kernel_ptr() {
+  return reinterpret_cast<const void*>(&batch_step_kernel<R, TY>);
+}
+
+const void* kernel_for(int R, int variant) {
+  const bool tall = variant == 0;
+  switch (R) {
+    case 1: return tall ? kernel_ptr<1, 64>() : kernel_ptr<1, 32>();
+    case 3: return tall ? kernel_ptr<3, 64>() : kernel_ptr<3, 32>();
+    case 5: return tall ? kernel_ptr<5, 64>() : kernel_ptr<5, 32>();
+    case 7: return tall ? kernel_ptr<7, 64>() : kernel_ptr<7, 32>();
+    default: return nullptr;
+  }
+}
+
+int threads_for(int variant) { return (TX / 4) * (batch_tile_y(variant) / RUN); }
+
+}  // namespace
+
+int batch_tile_y(int variant) { return variant == 0 ? 64 : 32; }
+
+size_t batch_smem(int R, int variant) {
+  return sizeof(float) * 2 * (size_t)BW * (batch_tile_y(variant) + 2 * R) + 16;
+}
+
+int batch_max_ctas(int R, int variant) {
+  const void* fn = kernel_for(R, variant);
+  if (!fn) return 0;
+  const size_t smem = batch_smem(R, variant);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_for(variant), smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per * sms;
+}
+
+cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st) {
+  if (a.active <= 0) return cudaSuccess;
+  const void* fn = kernel_for(R, variant);
+  if (!fn) return cudaErrorInvalidValue;
+  const int grid = nctas < a.active ? nctas : a.active;
+  void* args[] = {const_cast<BatchStepArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant)), args, batch_smem(R, variant), st);
+}
+
+cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map) {
+  auto fn = tma_encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)(batch_tile_y(variant) + 2 * R)};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace pat

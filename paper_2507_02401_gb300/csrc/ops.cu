@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "batch.h"
 #include "plan.h"
 
 namespace pat {
@@ -779,6 +780,18 @@ pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* 
     return PAT_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // one batched engine over all instances when they qualify and the arrays live on the device
+  bool dev = batch_eligible(plans, B);
+  for (int i = 0; dev && i < B; ++i) dev = ys[i] && xs[i] && is_device_ptr(ys[i]) && is_device_ptr(xs[i]);
+  if (dev) {
+    pat_batch* b = nullptr;
+    pat_status s = pat_batch_create(plans, B, stream, &b);
+    if (s == PAT_OK) {
+      s = pat_batch_solve(b, ys, alphas, ss, iters, xs, per_inst, stream);
+      pat_batch_destroy(b);
+    }
+    return s;
+  }
   pat_status first = PAT_OK;
   for (int i = 0; i < B; ++i) {
     pat_status s = pat_solve(plans[i], ys[i], alphas[i], ss[i], iters, nullptr, nullptr, xs[i], nullptr, stream);

@@ -118,3 +118,52 @@ class Plan:
         u0t = self._f32(u0) if u0 is not None else None
         _lib.pat_solve(self.handle, y, alpha, s, iters, u0t, u, x, log, self._stream(stream))
         return u, x, (log[:iters] if want_log else None)
+
+
+class Batch:
+    """Many 2D constant-medium plans advanced together by the batched engine
+    (one launch per time step over all instances' tiles; tile height chosen
+    by the library's autotuner when the batch is created).  The plans must
+    outlive the batch and are not used concurrently with it."""
+
+    def __init__(self, plans, stream=None):
+        self.plans = list(plans)
+        self.handle = _lib.pat_batch_create([p.handle for p in self.plans], stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pat_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        return stream if stream is not None else torch.cuda.current_stream()
+
+    @property
+    def info(self):
+        return _lib.pat_batch_info(self.handle)
+
+    def forward(self, xs, outs=None, stream=None):
+        """[K_i x_i] for every instance; returns a list of (Ns_i, nt_i) tensors."""
+        xs = [Plan._f32(x) for x in xs]
+        ys = outs or [torch.empty((p.ns, p.nt), device="cuda", dtype=torch.float32) for p in self.plans]
+        _lib.pat_batch_forward(self.handle, xs, ys, self._stream(stream))
+        return ys
+
+    def adjoint(self, ys, outs=None, stream=None):
+        ys = [Plan._f32(y) for y in ys]
+        xs = outs or [torch.empty(p.shape, device="cuda", dtype=torch.float32) for p in self.plans]
+        _lib.pat_batch_adjoint(self.handle, ys, xs, self._stream(stream))
+        return xs
+
+    def solve(self, ys, alphas, ss, iters, outs=None, stream=None):
+        """CG for every instance; returns (images, status, per-instance statuses)."""
+        ys = [Plan._f32(y) for y in ys]
+        xs = outs or [torch.empty(p.shape, device="cuda", dtype=torch.float32) for p in self.plans]
+        rc, per = _lib.pat_batch_solve(self.handle, ys, alphas, ss, iters, xs, self._stream(stream))
+        return xs, rc, per
