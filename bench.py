@@ -17,6 +17,11 @@ instance (weak scaling, no data-path collective).
 sensors on a sphere, 800 time samples, 3D db4 with 4 levels, 30 CG
 iterations per step).
 
+--workload batch64 times 64 independent reconstructions of uneven size
+(n in {128..512}, order 8, 50 CG iterations each) through the batched
+engine, one step = one batched solve, beside the same solves one after the
+other.
+
 --sweep prints one line per grid of the per-step engines' HBM sweep
 (2D 2048^2 .. 16384^2 x orders {2, 8}, 3D 256^3 and 512^3 order 4).
 
@@ -237,6 +242,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "batch64":
+        return run_reference_batch(args, world)
     w = synth.workload(args.workload)
     nt_s = WORKLOADS[args.workload]["oracle_nt"]
     if nt_s:
@@ -270,6 +277,45 @@ def run_reference(args):
             "config": {"workload": WORKLOADS[args.workload]["desc"], "step": step_desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": f"{args.steps} timed steps ({step_desc}) after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batch(args, world):
+    """Reference arm of the 64-instance workload: per size class one oracle
+    K + K* pair at 40 steps, scaled linearly to every instance's nt; a step
+    is one CG iteration of all 64 instances (wave work only)."""
+    import synth
+    import oracle
+    ws = synth.batched_workloads()
+    by_n = {}
+    for w in ws:
+        by_n.setdefault(w.shape[0], w)
+    nt_s = 40
+
+    def one_iteration():
+        per_pt = {}
+        for n, w in by_n.items():
+            wave = oracle.Wave(w.shape, w.h, w.dt, nt_s, w.order, w.c_array(), w.sensors)
+            t0 = time.perf_counter()
+            wave.adjoint(wave.forward(w.x_true))
+            per_pt[n] = (time.perf_counter() - t0) / (nt_s - 1)
+        return sum(per_pt[w.shape[0]] * (w.nt - 1) for w in ws)
+
+    for _ in range(args.warmup):
+        one_iteration()
+    dt = sum(one_iteration() for _ in range(args.steps))
+    value = args.steps * len(ws) / dt
+    step_desc = ("one oracle CG iteration of all 64 instances (K + K* per instance, timed per grid size at 40 "
+                 "steps and scaled linearly to each instance's nt)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "64 independent 2D reconstructions of uneven size (batched workload)",
+                       "step": step_desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} steps ({step_desc}) after {args.warmup} warm-up"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -461,6 +507,148 @@ def run_sweep(args):
     return 0
 
 
+def run_batch(args):
+    """64 independent reconstructions of uneven size through the batched
+    engine (one step = one 50-iteration batched solve of all instances),
+    against the same 64 solves one after the other with pat_solve."""
+    import torch
+
+    import synth
+    from paper_2507_02401_gb300 import Batch, Plan, _lib
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    rank, world, local = dist_setup(True)
+    ws = synth.batched_workloads(seed=1003 + rank)
+    iters = args.iters or ws[0].iters
+    plans = [Plan(w.shape, w.h, w.dt, w.nt, w.order, w.c, w.sensors, w.family, w.levels) for w in ws]
+    batch = Batch(plans)
+    stream = torch.cuda.current_stream()
+    ys = batch.forward([w.x_true for w in ws])
+    rng = np.random.default_rng(1234 + rank)
+    y_np = [synth.add_noise(y.cpu().numpy().astype(np.float64), w.noise, rng).astype(np.float32)
+            for y, w in zip(ys, ws)]
+    ys = [torch.as_tensor(y, device="cuda") for y in y_np]
+    ss = [w.s[0] for w in ws]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    vs = [torch.randn(p.N, device="cuda", generator=g) for p in plans]
+    vs = [v / v.norm() for v in vs]
+    for _ in range(args.power_iters):  # lambda_max of E_s* K* K E_s per instance, through the batch
+        hs = batch.adjoint(batch.forward([p.Es(v, s) for p, v, s in zip(plans, vs, ss)]))
+        hv = [p.EsT(h, s) for p, h, s in zip(plans, hs, ss)]
+        lams = [float(h.norm()) for h in hv]
+        vs = [h / lam for h, lam in zip(hv, lams)]
+    alphas = [w.alpha[0] * lam for w, lam in zip(ws, lams)]
+    xs = [torch.empty(w.shape, device="cuda") for w in ws]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+
+    def solve_batched():
+        rc, per = _lib.pat_batch_solve(batch.handle, ys, alphas, ss, iters, xs, stream)
+        assert rc == 0, (rc, per, _lib.load().pat_last_error())
+
+    for _ in range(args.warmup):
+        solve_batched()
+    torch.cuda.synchronize()
+    info = batch.info
+    # batched K alone (algorithmic bytes of the step kernel)
+    xs_in = [torch.as_tensor(w.x_true, dtype=torch.float32, device="cuda") for w in ws]
+    yk = [torch.empty((p.ns, p.nt), device="cuda") for p in plans]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _lib.pat_batch_forward(batch.handle, xs_in, yk, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k_ms = e0.elapsed_time(e1)
+    pts_k = sum(w.N * (w.nt - 1) for w in ws)
+    sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        solve_batched()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, True)
+    x_batched = [x.cpu().numpy() for x in xs]
+
+    # the plain single-instance path: the same 64 solves one after the other
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x_seq = []
+    s0.record(stream)
+    for p, y, a, s in zip(plans, ys, alphas, ss):
+        _, x1, _ = p.solve(y, a, s, iters, stream=stream)
+        x_seq.append(x1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    diffs = [float(np.linalg.norm(xb - xq.cpu().numpy()) / max(np.linalg.norm(xq.cpu().numpy()), 1e-30))
+             for xb, xq in zip(x_batched, x_seq)]
+
+    # end to end: host data in, images out, through the batched solve
+    y_host = [torch.as_tensor(y, dtype=torch.float32).pin_memory() for y in y_np]
+    x_host = [torch.empty(w.shape, dtype=torch.float32).pin_memory() for w in ws]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for yd, yh in zip(ys, y_host):
+            yd.copy_(yh, non_blocking=True)
+        solve_batched()
+        for xh, xd in zip(x_host, xs):
+            xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, True)
+
+    n_inst = len(ws)
+    iters_total = world * args.steps * n_inst * iters
+    peak, peak_kind = peaks()
+    achieved = 12.0 * pts_k / (k_ms / 1e3) / 1e9
+    max_nt = max(w.nt for w in ws)
+    line = {
+        "metric": METRIC, "value": iters_total / (t_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n_inst} independent 2D reconstructions, n in {{128,192,256,384,512}}, c = 1500, "
+                               f"order 8, nt = ceil(sqrt(2) n / 0.3), 64-512 sensors on circles or arcs, "
+                               f"alpha log-uniform in [1e-4, 1e-1] x lambda_max, s in {{1, 1.5, 2}}, db4 4 levels, "
+                               f"{iters} CG iterations each; one step = one batched solve of all instances",
+                   "engine": "batched", "tile_rows": info["tile_rows"], "ctas": info["ctas"],
+                   "autotune_ms": info["tune_ms"], "graph_nodes_per_iteration": info["graph_nodes"],
+                   "l2": "256 MiB buffer written before every step (inside the timed region)",
+                   "parallelism": f"replicas x{world} (independent batches per rank)"},
+        "solves_per_s": world * args.steps * n_inst / (t_ms / 1e3),
+        "sequential": {"solves_per_s": n_inst / (seq_ms / 1e3), "ms": seq_ms,
+                       "path": "pat_solve per instance (single-instance engines, FP64 CG scalars)"},
+        "speedup_vs_sequential": (world * args.steps * n_inst / (t_ms / 1e3)) / (n_inst / (seq_ms / 1e3)),
+        "max_rel_diff_vs_sequential": max(diffs),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "batch_step_kernel<R=7> (batched K)",
+                     "algorithmic_bytes_per_point_update": 12, "launch_ms": k_ms / max_nt,
+                     "launch": "one time step of every running instance (mean over a whole batched K)",
+                     "note": "the 64 instances' fields (~80 MB) are largely L2-resident"},
+        "e2e": {"value": iters_total / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(y.nbytes for y in y_np)),
+                "d2h_bytes_per_step": int(sum(w.N * 4 for w in ws))},
+        # graph nodes per CG iteration; right-hand side (batched K*, fills, E_s*, CG start) and final E_s; L2 flush
+        "gpu_launches": int(args.steps * (iters * info["graph_nodes"] + max_nt + 11 * n_inst + 1)),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    batch.close()
+    return 0
+
+
 def plan_varc(w):
     return np.ndim(w.c) != 0 and float(np.max(w.c)) != float(np.min(w.c))
 
@@ -471,7 +659,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default=WORKLOAD)
     ap.add_argument("--iters", type=int, default=0, help="override CG iterations per step")
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle CG iterations in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -485,6 +673,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_ours(args)
 
 
