@@ -466,8 +466,11 @@ def run_sweep(args):
     cases = [((n, n), o, False) for n in (2048, 4096, 8192, 16384) for o in (2, 8)]
     cases += [((4096, 4096), 8, True), ((256, 256, 256), 4, False), ((512, 512, 512), 4, False)]
     nt = 201
-    if args.only:
-        cases = [cs for cs in cases if "x".join(map(str, cs[0])) == args.only]
+    if args.only:  # a grid ("4096x4096") or one case ("4096x4096-o8", "4096x4096-o8v" for the varying medium)
+        def ids(cs):
+            g = "x".join(map(str, cs[0]))
+            return {g, f"{g}-o{cs[1]}" + ("v" if cs[2] else "")}
+        cases = [cs for cs in cases if args.only in ids(cs)]
     for shape, order, varc in cases:
         h = 1e-4
         rng = np.random.default_rng(0)
@@ -664,7 +667,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle CG iterations in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--power-iters", type=int, default=20, help="power iterations for lambda_max")
-    ap.add_argument("--only", default="", help="with --sweep: run only the grid named like 256x256x256")
+    ap.add_argument("--only", default="", help="with --sweep: run only a grid (256x256x256) or a case (4096x4096-o8)")
     ap.add_argument("--sweep", action="store_true",
                     help="time the per-step wave engines on 2D 2048^2..16384^2 (orders 2, 8) and 3D grids instead")
     args = ap.parse_args()
