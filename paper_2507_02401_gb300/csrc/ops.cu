@@ -89,17 +89,39 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
   if (p->dim == 2 && p->tma2d && !(adj && p->varc) && tma_ready(p, a)) {
     // forward, and the constant-medium adjoint (same recurrence): TMA tile pipelines
     const bool varc = p->varc && !adj;
-    const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, varc);
+    // injection fused for radius <= 3; at radius 5-7 the fused variant's code generation is slower than
+    // mode 0 plus a separate injection launch on every grid measured (2048^2 .. 16384^2)
+    const bool fuse = a.inj_r && p->R <= 3;
+    const int mode = varc ? 1 : (fuse ? 2 : 0);
+    const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, mode);
     if (y && a.ns > nthr) a.y = nullptr;
     const pat_plan::TmaDesc* dp = tma_desc(p, a.cur);
     if (!dp) return cudaErrorInvalidValue;
     StepArgs b = a;
     if (!varc) b.kappa = b.kappa_lo = nullptr;
-    e = step2d_tma_launch(p->R, varc, b, dp->halo, p->d_status, p->timeout_ns, st);
+    if (fuse) {  // injection fused per tile
+      b.inj_tile_ptr = p->d_tinj2_ptr;
+      b.inj_tile = p->d_tinj2;
+      b.ent_sensor = p->d_ent_sensor;
+      b.ent_w = p->d_ent_w;
+    } else if (a.inj_r) {
+      e = inject_launch(a.dbuf, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, a.inj_r, p->nt,
+                        a.inj_t, 1.f, st);
+      if (e != cudaSuccess) return e;
+      b.inj_r = nullptr;
+    }
+    e = step2d_tma_launch(p->R, mode, b, dp->halo, p->d_status, p->timeout_ns, st);
   } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;
-    e = step2d_launch(p->R, adj, a, st);
+    if (a.inj_r) {
+      e = inject_launch(a.dbuf, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, a.inj_r, p->nt,
+                        a.inj_t, 1.f, st);
+      if (e != cudaSuccess) return e;
+    }
+    StepArgs b = a;
+    b.inj_r = nullptr;
+    e = step2d_launch(p->R, adj, b, st);
   } else if (p->tma3d && tma_ready(p, a)) {
     const long long nthr = tma3d_threads(p->n[0], p->n[1], p->n[2], p->tma3d_zchunk);
     if (y && a.ns > nthr) a.y = nullptr;
@@ -203,8 +225,9 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
     PAT_TRY_CUDA(fill_launch(Qlo(nt), p->N, 0.f, st));
     a.dbuf = G;
     a.dbuf_lo = p->d_wv[5];
+    a.inj_r = y;  // G^{m+1} + S^T r_m, injected by (or just before) each step
     for (int m = nt - 1; m >= 1; --m) {
-      PAT_TRY_CUDA(inject(G, m));  // G^{m+1} + S^T r_m
+      a.inj_t = m;
       a.cur = Qbuf(m + 1);
       a.cur_lo = Qlo(m + 1);
       a.next = Qbuf(m);
@@ -214,7 +237,7 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
       a.c_lap = 1.f;
       PAT_TRY_CUDA(step_launch(p, true, a, st));
     }
-    PAT_TRY_CUDA(inject(G, 0));
+    a.inj_t = 0;
     a.cur = Qbuf(1);
     a.cur_lo = Qlo(1);
     a.next = x;
@@ -266,6 +289,7 @@ static long long wave_kernels(const pat_plan* p, bool adj) {
   if (nt == 1) return adj ? 2 : 1;
   if (!adj) return nt;  // nt-1 steps + final sample
   const long long inj = p->n_inj > 0 ? 1 : 0;
+  if (p->dim == 2 && p->tma2d && !p->varc && p->R <= 3) return 4 + (nt - 1) + 1;  // 4 fills, fused injection
   if (p->dim == 2) return 4 + (nt - 1) * (1 + inj) + (1 + inj);  // 4 fills, (inject+step) x (nt-1), final
   return (1 + inj) + (nt - 2) * (1 + inj) + (1 + inj);             // fill+inject, (step+inject), final
 }
@@ -531,8 +555,9 @@ pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float*
     PAT_TRY_CUDA(fill_launch(Qlo(nt), N, 0.f, st));
     c.dbuf = G;
     c.dbuf_lo = p->d_wv[5];
+    c.inj_r = r;
     for (int m = nt - 1; m >= 1; --m) {
-      PAT_TRY_CUDA(inject(G, m));
+      c.inj_t = m;
       c.cur = Qbuf(m + 1);
       c.cur_lo = Qlo(m + 1);
       c.next = Qbuf(m);

@@ -49,16 +49,22 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
   a.y[(long long)s * a.nt + a.t_sample] = v;
 }
 
-template <int R, bool VARC>
+// MODE 0: constant medium; 1: varying medium (forward); 2: constant medium with the adjoint's
+// injection S^T r_m fused (a separate instance, so the other modes keep their code generation)
+template <int R, int MODE>
 __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
                                                              int* status, long long timeout_ns) {
   using G = G2<R>;
+  constexpr bool VARC = MODE == 1, INJ = MODE == 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
+  float* injt = stage0 + 2 * G::STAGE + 4;  // INJ: TX x TY injection tile after the barriers (16-byte aligned)
 
   const int t = threadIdx.x;
   fused_sample2(a, (long long)blockIdx.x * THREADS + t);
+  if (INJ)
+    for (int i = t; i < TX * TY / 4; i += THREADS) reinterpret_cast<float4*>(injt)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   const int nx = a.nx, ny = a.ny;
   const int tiles_x = (nx + TX - 1) / TX;
@@ -115,6 +121,18 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
         kl4[rr] = kh4[rr];
       }
     }
+    int inj_b = 0, inj_e = 0;
+    if (INJ) {  // adjoint: S^T r_m of the tile's injected cells into the shared tile (each cell listed once)
+      inj_b = a.inj_tile_ptr[tile];
+      inj_e = a.inj_tile_ptr[tile + 1];
+      for (int e = inj_b + t; e < inj_e; e += THREADS) {
+        const InjCell c = a.inj_tile[e];  // .local = ly * 64 + lx within the tile
+        float v = 0.f;
+        for (int q = c.beg; q < c.end; ++q)
+          v = fmaf(a.ent_w[q], a.inj_r[(long long)a.ent_sensor[q] * a.nt + a.inj_t], v);
+        injt[c.local] = v;
+      }
+    }
     const bool good = mbar_wait(&bars[s], (k >> 1) & 1, timeout_ns);
     if (__syncthreads_or(!good)) {
       if (t == 0) atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -122,6 +140,18 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       break;
     }
     const float* P = stage0 + s * G::STAGE;
+    if (INJ && inj_e > inj_b) {  // G += S^T r_m in the owners' registers; the shared tile is cleared again
+#pragma unroll
+      for (int rr = 0; rr < RUN; ++rr) {
+        float4* q = reinterpret_cast<float4*>(injt + (r0 + rr) * TX + c0);
+        const float4 v = *q;
+        d4[rr].x += v.x;
+        d4[rr].y += v.y;
+        d4[rr].z += v.z;
+        d4[rr].w += v.w;
+        *q = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
 
     // sliding window over this thread's 4 columns: win[i] = box row (row - R + i)
     float4 win[2 * R + 1];
@@ -176,30 +206,32 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
     for (int j = max(0, issued - 2); j < issued; ++j) mbar_wait(&bars[j & 1], (j >> 1) & 1, timeout_ns);
 }
 
-template <int R, bool VARC>
-cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mp, int nctas, int* status,
-                     long long timeout_ns, cudaStream_t st) {
-  const size_t smem = G2<R>::SMEM;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(step2d_tma_kernel<R, VARC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
-  step2d_tma_kernel<R, VARC><<<nctas, THREADS, smem, st>>>(a, mp, status, timeout_ns);
-  return cudaGetLastError();
+template <int R, int MODE>
+const void* kfn() {
+  return reinterpret_cast<const void*>(&step2d_tma_kernel<R, MODE>);
 }
 
-template <bool VARC>
-cudaError_t launch_v(int R, const StepArgs& a, const CUtensorMap& mp, int nctas, int* status,
-                     long long timeout_ns, cudaStream_t st) {
-  switch (R) {
-    case 1: return launch_r<1, VARC>(a, mp, nctas, status, timeout_ns, st);
-    case 3: return launch_r<3, VARC>(a, mp, nctas, status, timeout_ns, st);
-    case 5: return launch_r<5, VARC>(a, mp, nctas, status, timeout_ns, st);
-    case 7: return launch_r<7, VARC>(a, mp, nctas, status, timeout_ns, st);
-    default: return cudaErrorInvalidValue;
+const void* kernel_for(int R, int mode) {
+  switch (R * 4 + mode) {
+    case 4 + 0: return kfn<1, 0>();
+    case 4 + 1: return kfn<1, 1>();
+    case 4 + 2: return kfn<1, 2>();
+    case 12 + 0: return kfn<3, 0>();
+    case 12 + 1: return kfn<3, 1>();
+    case 12 + 2: return kfn<3, 2>();
+    case 20 + 0: return kfn<5, 0>();
+    case 20 + 1: return kfn<5, 1>();
+    case 20 + 2: return kfn<5, 2>();
+    case 28 + 0: return kfn<7, 0>();
+    case 28 + 1: return kfn<7, 1>();
+    case 28 + 2: return kfn<7, 2>();
+    default: return nullptr;
   }
+}
+
+size_t smem_for(int R, int mode) {
+  const size_t base = R == 1 ? G2<1>::SMEM : R == 3 ? G2<3>::SMEM : R == 5 ? G2<5>::SMEM : G2<7>::SMEM;
+  return base + (mode == 2 ? sizeof(float) * TX * TY : 0);
 }
 
 }  // namespace
@@ -225,19 +257,19 @@ cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* 
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Persistent grid: as many CTAs as fit (2 per SM at order 8), at most one per tile.
-int tma2d_ctas(int nx, int ny, int R, bool varc) {
-  static int cached[2][8] = {{0}};
-  int& c = cached[varc ? 1 : 0][R];
+// Persistent grid: as many CTAs as fit on the device, at most one per tile.
+int tma2d_ctas(int nx, int ny, int R, int mode) {
+  static int cached[3][8] = {{0}};
+  int& c = cached[mode][R];
   if (!c) {
     int dev = 0, sms = 148, per = 1;
+    const void* fn = kernel_for(R, mode);
+    const size_t smem = smem_for(R, mode);
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = R == 1 ? G2<1>::SMEM : R == 3 ? G2<3>::SMEM : R == 5 ? G2<5>::SMEM : G2<7>::SMEM;
-    const void* fn = R == 1   ? (varc ? (const void*)step2d_tma_kernel<1, true> : (const void*)step2d_tma_kernel<1, false>)
-                     : R == 3 ? (varc ? (const void*)step2d_tma_kernel<3, true> : (const void*)step2d_tma_kernel<3, false>)
-                     : R == 5 ? (varc ? (const void*)step2d_tma_kernel<5, true> : (const void*)step2d_tma_kernel<5, false>)
-                              : (varc ? (const void*)step2d_tma_kernel<7, true> : (const void*)step2d_tma_kernel<7, false>);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // mode 2 holds 16 KB more shared memory per CTA: ask for the largest carveout so that three CTAs
+    // fit an SM (modes 0 and 1 run faster with the default split, which leaves L1 larger)
+    if (mode == 2) cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, THREADS, smem) != cudaSuccess || per < 1) {
       cudaGetLastError();
       per = 1;
@@ -248,13 +280,17 @@ int tma2d_ctas(int nx, int ny, int R, bool varc) {
   return ntiles < c ? ntiles : c;
 }
 
-long long tma2d_threads(int nx, int ny, int R, bool varc) { return (long long)tma2d_ctas(nx, ny, R, varc) * THREADS; }
+long long tma2d_threads(int nx, int ny, int R, int mode) { return (long long)tma2d_ctas(nx, ny, R, mode) * THREADS; }
 
-cudaError_t step2d_tma_launch(int R, bool varc, const StepArgs& a, const CUtensorMap& p, int* status,
+cudaError_t step2d_tma_launch(int R, int mode, const StepArgs& a, const CUtensorMap& p, int* status,
                               long long timeout_ns, cudaStream_t st) {
-  const int nctas = tma2d_ctas(a.nx, a.ny, R, varc);
-  return varc ? launch_v<true>(R, a, p, nctas, status, timeout_ns, st)
-              : launch_v<false>(R, a, p, nctas, status, timeout_ns, st);
+  const void* fn = kernel_for(R, mode);
+  if (!fn) return cudaErrorInvalidValue;
+  const int nctas = tma2d_ctas(a.nx, a.ny, R, mode);  // sets the kernel's attributes once
+  CUtensorMap map = p;
+  StepArgs args = a;
+  void* params[] = {&args, &map, &status, &timeout_ns};
+  return cudaLaunchKernel(fn, dim3(nctas), dim3(THREADS), params, smem_for(R, mode), st);
 }
 
 }  // namespace pat
