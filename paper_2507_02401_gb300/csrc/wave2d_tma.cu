@@ -178,12 +178,12 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       for (int j = 0; j < 4; ++j) {
         const float c = f[8 + j];
         const float c2 = c + c;
-        float acc = 0.f;
+        float acc = 0.f;  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
 #pragma unroll
         for (int m = 1; m <= R; ++m)
-          acc = fmaf(a.w[m], pair_term<true>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
+          acc = fmaf(a.w[m], pair_term<false>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
 #pragma unroll
-        for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<true>(f[8 + j + m], f[8 + j - m], c, c2), acc);
+        for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<false>(f[8 + j + m], f[8 + j - m], c, c2), acc);
         float inc;
         if (VARC)
           inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
