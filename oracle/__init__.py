@@ -12,6 +12,6 @@ seeded input generators of `synth`.
   solve.py          CG on (E_s* K* K E_s + alpha I) u = E_s* K* y, paper
                     Eq. (linear_minimization) in coefficient form
 """
-from .fdtd import Wave, set_threads, max_threads  # noqa: F401
+from .fdtd import Wave, set_threads, max_threads, sponge_sigma, sponge_sigma_max  # noqa: F401
 from .wavelet import Wavelet, daubechies, highpass  # noqa: F401
 from .solve import cg, normal_op, rhs, Breakdown  # noqa: F401

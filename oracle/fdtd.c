@@ -23,6 +23,16 @@
  * with the standard staggered Fornberg weights c_k; -G^T is the matching
  * divergence.  Faces exist wherever they can touch an interior cell.
  *
+ * Absorbing layer (optional; the build's reading of the paper's PML, which the
+ * paper takes from k-Wave): a damping rate sigma(x) >= 0 [1/s] enters the
+ * pressure equation, p_t + sigma p = -c^2 div v, with sigma p averaged over
+ * the two time levels (trapezoidal rule):
+ *
+ *   P^{n} = alpha .* P^{n-1} + beta .* (c^2 dt/h) (G^T v^{n-1/2}),
+ *   alpha = (1 - sigma dt/2) / (1 + sigma dt/2),  beta = 1 / (1 + sigma dt/2),
+ *
+ * which reduces to the undamped program for sigma = 0.
+ *
  * Sampling (the point-sensor trace of Sec. 2.2): y[s, n] = sum of the
  * bilinear (2D) / trilinear (3D) interpolation weights of sensor s times
  * P^n at the 2^d surrounding cells, for n = 0 .. nt-1 (P^0 included).
@@ -160,17 +170,19 @@ typedef struct {
   int nt, ns;
   double dt, h;
   double* b;  /* c^2 dt / h on padded cells (0 in the pad) */
+  double* alpha;  /* damping of P (NULL: none) */
+  double* beta;   /* damping of the update (NULL: none) */
   sensor_t* sens;
 } problem;
 
 static int problem_init(problem* pb, int dim, const int* n, double h, double dt, int nt, int order,
                         const double* c, int ns, const double* sensors) {
+  memset(pb, 0, sizeof(*pb));
   if (dim != 2 && dim != 3) return -1;
   if (order != 2 && order != 4 && order != 6 && order != 8) return -1;
   if (nt < 1 || ns < 0) return -1;
   for (int a = 0; a < dim; ++a)
     if (n[a] < 2) return -1;
-  memset(pb, 0, sizeof(*pb));
   geom_init(&pb->g, dim, n, order / 2);
   pb->nt = nt;
   pb->ns = ns;
@@ -193,7 +205,29 @@ static int problem_init(problem* pb, int dim, const int* n, double h, double dt,
 
 static void problem_free(problem* pb) {
   free(pb->b);
+  free(pb->alpha);
+  free(pb->beta);
   free(pb->sens);
+}
+
+/* alpha, beta from the damping rate sigma (N cells, 1/s); NULL leaves the program undamped. */
+static int set_damping(problem* pb, const double* sigma) {
+  if (!sigma) return 0;
+  const geom* g = &pb->g;
+  pb->alpha = (double*)calloc((size_t)g->total, sizeof(double));
+  pb->beta = (double*)calloc((size_t)g->total, sizeof(double));
+  if (!pb->alpha || !pb->beta) return -2;
+  for (long i = 0; i < g->total; ++i) pb->alpha[i] = pb->beta[i] = 1.0;
+  for (int z = 0; z < g->n[2]; ++z)
+    for (int y = 0; y < g->n[1]; ++y)
+      for (int x = 0; x < g->n[0]; ++x) {
+        const double sg = sigma[((long)z * g->n[1] + y) * g->n[0] + x];
+        if (!(sg >= 0.0)) return -4;
+        const double q = 0.5 * sg * pb->dt;
+        pb->alpha[pidx(g, x, y, z)] = (1.0 - q) / (1.0 + q);
+        pb->beta[pidx(g, x, y, z)] = 1.0 / (1.0 + q);
+      }
+  return 0;
 }
 
 static void sample(const problem* pb, const double* P, double* y, int n) {
@@ -223,13 +257,18 @@ static void from_padded(const geom* g, const double* P, double* x) {
       memcpy(x + ((long)z * g->n[1] + y) * g->n[0], P + pidx(g, 0, y, z), sizeof(double) * g->n[0]);
 }
 
-/* P[interior] += b .* (sum_a G_a^T V_a) */
+/* P[interior] = alpha .* P + beta .* b .* (sum_a G_a^T V_a)   (alpha = beta = 1 without damping) */
 static void pressure_update(const problem* pb, double* const* V, double* P, double* tmp) {
   const geom* g = &pb->g;
   memset(tmp, 0, sizeof(double) * g->total);
   for (int a = 0; a < g->dim; ++a) gradT_axis(g, a, V[a], tmp, 1.0);
+  if (pb->alpha) {
 #pragma omp parallel for schedule(static)
-  for (long i = 0; i < g->total; ++i) P[i] += pb->b[i] * tmp[i];
+    for (long i = 0; i < g->total; ++i) P[i] = pb->alpha[i] * P[i] + pb->beta[i] * pb->b[i] * tmp[i];
+  } else {
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < g->total; ++i) P[i] += pb->b[i] * tmp[i];
+  }
 }
 
 void oracle_set_threads(int nthreads) {
@@ -248,11 +287,13 @@ int oracle_max_threads(void) {
 #endif
 }
 
-/* y = K x.  x: N cells; y: ns*nt (sensor-major). Returns 0 on success. */
-int oracle_forward(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
-                   const double* sensors, const double* x, double* y) {
+/* y = K x with the damping rate sigma (N cells, or NULL).  x: N cells; y: ns*nt (sensor-major).
+ * Returns 0 on success. */
+int oracle_forward_damped(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
+                          const double* sensors, const double* sigma, const double* x, double* y) {
   problem pb;
   int rc = problem_init(&pb, dim, n, h, dt, nt, order, c, ns, sensors);
+  if (!rc) rc = set_damping(&pb, sigma);
   if (rc) {
     problem_free(&pb);
     return rc;
@@ -278,11 +319,17 @@ int oracle_forward(int dim, const int* n, double h, double dt, int nt, int order
   return 0;
 }
 
-/* x = K* y, the reverse sweep of oracle_forward. */
-int oracle_adjoint(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
-                   const double* sensors, const double* y, double* x) {
+int oracle_forward(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
+                   const double* sensors, const double* x, double* y) {
+  return oracle_forward_damped(dim, n, h, dt, nt, order, c, ns, sensors, NULL, x, y);
+}
+
+/* x = K* y, the reverse sweep of oracle_forward_damped. */
+int oracle_adjoint_damped(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
+                          const double* sensors, const double* sigma, const double* y, double* x) {
   problem pb;
   int rc = problem_init(&pb, dim, n, h, dt, nt, order, c, ns, sensors);
+  if (!rc) rc = set_damping(&pb, sigma);
   if (rc) {
     problem_free(&pb);
     return rc;
@@ -303,9 +350,18 @@ int oracle_adjoint(int dim, const int* n, double h, double dt, int nt, int order
     }
     /* transpose of  y_step = S P^step */
     inject(&pb, y, Pb, step);
-    /* transpose of  P^step = P^{step-1} + b .* G^T v : v_bar += G (b .* P_bar) */
+    /* transpose of  P^step = alpha .* P^{step-1} + beta .* b .* G^T v :
+     * v_bar += G (beta .* b .* P_bar), then P_bar <- alpha .* P_bar */
+    if (pb.alpha) {
 #pragma omp parallel for schedule(static)
-    for (long i = 0; i < g->total; ++i) bP[i] = pb.b[i] * Pb[i];
+      for (long i = 0; i < g->total; ++i) {
+        bP[i] = pb.beta[i] * pb.b[i] * Pb[i];
+        Pb[i] *= pb.alpha[i];
+      }
+    } else {
+#pragma omp parallel for schedule(static)
+      for (long i = 0; i < g->total; ++i) bP[i] = pb.b[i] * Pb[i];
+    }
     for (int a = 0; a < dim; ++a) grad_axis(g, a, bP, Vb[a], 1.0);
   }
   inject(&pb, y, Pb, 0);
@@ -323,7 +379,12 @@ int oracle_adjoint(int dim, const int* n, double h, double dt, int nt, int order
   return 0;
 }
 
-/* Medium gradient: g = d<r, K x>/d kappa per cell, kappa = (c dt/h)^2.
+int oracle_adjoint(int dim, const int* n, double h, double dt, int nt, int order, const double* c, int ns,
+                   const double* sensors, const double* y, double* x) {
+  return oracle_adjoint_damped(dim, n, h, dt, nt, order, c, ns, sensors, NULL, y, x);
+}
+
+/* Medium gradient: g = d<r, K x>/d kappa per cell, kappa = (c dt/h)^2 (undamped program).
  *
  * kappa enters the program only through b = c^2 dt / h = kappa h / dt in
  * P^n = P^{n-1} + b .* (G^T v^{n-1/2}).  Reversing the program as in
@@ -398,11 +459,13 @@ int oracle_kappa_grad(int dim, const int* n, double h, double dt, int nt, int or
 }
 
 /* Full wavefield history for small problems: P^n for n = 0..nt-1 into
- * hist[n*N + cell].  Used by the energy and closed-form checks. */
-int oracle_forward_history(int dim, const int* n, double h, double dt, int nt, int order, const double* c,
-                           const double* x, double* hist) {
+ * hist[n*N + cell], with the damping rate sigma (or NULL).  Used by the
+ * energy and closed-form checks. */
+int oracle_forward_history_damped(int dim, const int* n, double h, double dt, int nt, int order, const double* c,
+                                  const double* sigma, const double* x, double* hist) {
   problem pb;
   int rc = problem_init(&pb, dim, n, h, dt, nt, order, c, 0, NULL);
+  if (!rc) rc = set_damping(&pb, sigma);
   if (rc) {
     problem_free(&pb);
     return rc;
@@ -427,4 +490,9 @@ int oracle_forward_history(int dim, const int* n, double h, double dt, int nt, i
   free(tmp);
   problem_free(&pb);
   return 0;
+}
+
+int oracle_forward_history(int dim, const int* n, double h, double dt, int nt, int order, const double* c,
+                           const double* x, double* hist) {
+  return oracle_forward_history_damped(dim, n, h, dt, nt, order, c, NULL, x, hist);
 }
