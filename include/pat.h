@@ -248,6 +248,26 @@ typedef enum { PAT_PATH_AUTO = 0, PAT_PATH_PERSISTENT = 1, PAT_PATH_STEP = 2 } p
 pat_status pat_plan_set_path(pat_plan* plan, int path);
 pat_status pat_plan_get_path(const pat_plan* plan, int* path);
 
+/*
+ * pat_plan_set_sponge — absorbing layer of `width` cells along every face of
+ * a 2D grid (width = 0 removes it).  The paper's simulations absorb outgoing
+ * waves with a perfectly matched layer of 10 grid points (Sec. 5); this
+ * library's reading is a damping term in the pressure equation,
+ * p_t + sigma(x) p = -c^2 div v, with sigma p averaged over the two time
+ * levels, which changes the eliminated update to
+ *   D^{n+1} = a D^n + b kappa L P^n,   a = (1-q)/(1+q), b = 1/(1+q), q = sigma dt/2
+ * (first step D^1 = (a-1) P^0 + b kappa/2 L P^0), with K* its exact transpose.
+ * Profile: sigma = sigma_max ((width - d)/width)^2 within `width` cells of a
+ * face (d = cells to that face), summed over the two axes.
+ *   sigma_max  damping rate at the faces [1/s]; 0 selects
+ *              3 c_max ln(1e3) / (2 width h) (nominal reflection 1e-3).
+ * The persistent engine has no layer: while one is set the plan runs the
+ * per-step engine; the medium gradient and batches reject such plans.
+ * Errors: PAT_ERR_INVALID for 3D plans, width < 0, 2 width > nx or ny, or a
+ * negative / non-finite sigma_max.  Synchronises `stream`.
+ */
+pat_status pat_plan_set_sponge(pat_plan* plan, int width, double sigma_max, void* stream);
+
 /* Bound (nanoseconds, default 2e9) on any single inter-tile wait inside the
  * persistent engine; when it runs out the call ends early and
  * pat_plan_check() reports PAT_ERR_TIMEOUT. */

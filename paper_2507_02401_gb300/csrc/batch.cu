@@ -50,6 +50,7 @@ const char* ineligible(const pat_plan* p, int R) {
   if (p->varc) return "batched instances have a constant medium";
   if (p->R != R) return "batched instances share one stencil order";
   if (p->n[0] % 4 != 0) return "batched instances have nx divisible by 4";
+  if (p->sponge_w > 0) return "batched instances have no absorbing layer";
   return nullptr;
 }
 

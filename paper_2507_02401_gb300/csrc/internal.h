@@ -116,6 +116,11 @@ struct StepArgs {
   // 2D adjoint: injection S^T r_{inj_t} into dbuf before the step (nullptr = none).  The TMA kernel
   // fuses it through per-tile lists (64 x 64 tiles, InjCell.local = ly * 64 + lx within the tile);
   // otherwise a separate injection kernel runs first.
+  // 2D absorbing layer (nullptr = none): per-cell factors a, b of the damped update and the layer
+  // width in cells (tiles farther than that from every face skip the factors)
+  const float* sp_a;
+  const float* sp_b;
+  int sp_w;
   const float* inj_r;
   int inj_t;
   const int* inj_tile_ptr;
@@ -149,9 +154,10 @@ cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, 
 bool tma2d_supported(int nx, int R);
 // P boxes (80 x (64+2R)) and own-tile boxes (64 x 64) of an nx x ny float field
 cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* halo, CUtensorMap* own);
-// mode 0: constant medium, 1: varying medium (forward), 2: constant medium with fused injection (adjoint)
-long long tma2d_threads(int nx, int ny, int R, int mode);  // threads of one launch (fused sampling)
-cudaError_t step2d_tma_launch(int R, int mode, const StepArgs& a, const CUtensorMap& p, int* status,
+// mode 0: constant medium, 1: varying medium (forward), 2: constant medium with fused injection (adjoint);
+// sp 0: no absorbing layer, 1: layer with the forward update, 2: layer with the adjoint update
+long long tma2d_threads(int nx, int ny, int R, int mode, int sp);  // threads of one launch (fused sampling)
+cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, int* status,
                               long long timeout_ns, cudaStream_t st);
 
 // wave_step.cu

@@ -59,6 +59,11 @@ static StepArgs step_args(pat_plan* p) {
   a.sens_cell = p->d_sens_cell;
   a.sens_w = p->d_sens_w;
   a.corners = p->corners;
+  if (p->sponge_w > 0) {
+    a.sp_a = p->d_sp_a;
+    a.sp_b = p->d_sp_b;
+    a.sp_w = p->sponge_w;
+  }
   return a;
 }
 
@@ -93,7 +98,8 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     // mode 0 plus a separate injection launch on every grid measured (2048^2 .. 16384^2)
     const bool fuse = a.inj_r && p->R <= 3;
     const int mode = varc ? 1 : (fuse ? 2 : 0);
-    const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, mode);
+    const int sp = p->sponge_w > 0 ? (adj ? 2 : 1) : 0;
+    const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, mode, sp);
     if (y && a.ns > nthr) a.y = nullptr;
     const pat_plan::TmaDesc* dp = tma_desc(p, a.cur);
     if (!dp) return cudaErrorInvalidValue;
@@ -110,7 +116,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
       if (e != cudaSuccess) return e;
       b.inj_r = nullptr;
     }
-    e = step2d_tma_launch(p->R, mode, b, dp->halo, p->d_status, p->timeout_ns, st);
+    e = step2d_tma_launch(p->R, mode, sp, b, dp->halo, p->d_status, p->timeout_ns, st);
   } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;
@@ -831,6 +837,10 @@ pat_status pat_grad_kappa(pat_plan* plan, const float* x, const float* r, float*
   PAT_TRY(check_plan(plan));
   if (!x || !g || (!r && plan->ns > 0) || segment < 0) {
     set_error("x, r and g must not be NULL and segment >= 0");
+    return PAT_ERR_INVALID;
+  }
+  if (plan->sponge_w > 0) {
+    set_error("the medium gradient is defined for plans without an absorbing layer");
     return PAT_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)stream;

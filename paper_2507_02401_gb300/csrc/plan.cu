@@ -569,11 +569,13 @@ pat_status pat_plan_set_path(pat_plan* plan, int path) {
     set_error("plan is NULL");
     return PAT_ERR_INVALID;
   }
+  const bool persist = plan->persist_ok && plan->sponge_w == 0;
   if (path == PAT_PATH_AUTO) {
-    plan->path = plan->persist_ok ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
+    plan->path = persist ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
   } else if (path == PAT_PATH_PERSISTENT) {
-    if (!plan->persist_ok) {
-      set_error("the persistent engine is not available for this plan (3D, or too many tiles to co-reside)");
+    if (!persist) {
+      set_error("the persistent engine is not available for this plan (3D, too many tiles to co-reside, "
+                "or an absorbing layer)");
       return PAT_ERR_INVALID;
     }
     plan->path = path;
@@ -583,6 +585,63 @@ pat_status pat_plan_set_path(pat_plan* plan, int path) {
     set_error("unknown path %d", path);
     return PAT_ERR_INVALID;
   }
+  return PAT_OK;
+}
+
+pat_status pat_plan_set_sponge(pat_plan* plan, int width, double sigma_max, void* stream) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return PAT_ERR_INVALID;
+  }
+  if (width < 0 || !std::isfinite(sigma_max) || sigma_max < 0.0) {
+    set_error("absorbing layer: width >= 0 and a finite sigma_max >= 0 are required");
+    return PAT_ERR_INVALID;
+  }
+  if (width > 0 && plan->dim != 2) {
+    set_error("the absorbing layer is implemented for 2D grids");
+    return PAT_ERR_INVALID;
+  }
+  const int nx = plan->n[0], ny = plan->n[1];
+  if (width > 0 && (2 * width > nx || 2 * width > ny)) {
+    set_error("absorbing layer of %d cells does not fit a %d x %d grid", width, nx, ny);
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (width == 0) {
+    plan->sponge_w = 0;
+    plan->sponge_sigma_max = 0.0;
+    plan->path = plan->persist_ok ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
+    const char* env = getenv("PAT_WAVE_PATH");
+    if (env && strcmp(env, "step") == 0) plan->path = PAT_PATH_STEP;
+    return PAT_OK;
+  }
+  // quadratic profile: within `width` cells of a face sigma = sigma_max ((width - d) / width)^2,
+  // d = cells to that face; the axes' contributions add (corners twice).  Default sigma_max for a
+  // nominal reflection of 1e-3: 3 c_max ln(1e3) / (2 width h).
+  const double smax = sigma_max > 0.0 ? sigma_max : 3.0 * plan->c_max * std::log(1e3) / (2.0 * width * plan->h);
+  if (!plan->d_sp_a) {
+    PAT_TRY(plan_alloc(plan, reinterpret_cast<void**>(&plan->d_sp_a), sizeof(float) * plan->N, "layer factors"));
+    PAT_TRY(plan_alloc(plan, reinterpret_cast<void**>(&plan->d_sp_b), sizeof(float) * plan->N, "layer factors"));
+  }
+  std::vector<float> fa((size_t)plan->N), fb((size_t)plan->N);
+  auto prof = [&](int i, int n) {
+    const int d = std::min(i, n - 1 - i);
+    if (d >= width) return 0.0;
+    const double r = double(width - d) / width;
+    return smax * r * r;
+  };
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const double q = 0.5 * (prof(x, nx) + prof(y, ny)) * plan->dt;
+      fa[(size_t)y * nx + x] = (float)((1.0 - q) / (1.0 + q));
+      fb[(size_t)y * nx + x] = (float)(1.0 / (1.0 + q));
+    }
+  PAT_TRY_CUDA(cudaMemcpyAsync(plan->d_sp_a, fa.data(), sizeof(float) * plan->N, cudaMemcpyHostToDevice, st));
+  PAT_TRY_CUDA(cudaMemcpyAsync(plan->d_sp_b, fb.data(), sizeof(float) * plan->N, cudaMemcpyHostToDevice, st));
+  PAT_TRY_CUDA(cudaStreamSynchronize(st));
+  plan->sponge_w = width;
+  plan->sponge_sigma_max = smax;
+  plan->path = PAT_PATH_STEP;  // the persistent engine has no absorbing layer
   return PAT_OK;
 }
 

@@ -53,6 +53,11 @@ struct pat_plan {
   long long timeout_ns = 2000000000LL;
   int poll_ns = 0;  // exchange polling back-off
   float* d_wv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per-step engine fields
+  // absorbing layer (2D): width in cells (0 = none), damping rate at the faces [1/s], per-cell factors
+  int sponge_w = 0;
+  double sponge_sigma_max = 0.0;
+  float* d_sp_a = nullptr;
+  float* d_sp_b = nullptr;
   bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
   int tma3d_zchunk = 0;
   bool tma2d = false;  // 2D steps through the TMA tile-pipeline kernel (where it applies)

@@ -50,8 +50,13 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
 }
 
 // MODE 0: constant medium; 1: varying medium (forward); 2: constant medium with the adjoint's
-// injection S^T r_m fused (a separate instance, so the other modes keep their code generation)
-template <int R, int MODE>
+// injection S^T r_m fused (a separate instance, so the other modes keep their code generation).
+// SP 0: no absorbing layer; 1: layer, forward update; 2: layer, adjoint update.  With the layer's
+// per-cell factors a = (1-q)/(1+q), b = 1/(1+q), q = sigma dt/2:
+//   forward  D' = a D + b inc (first step: D' = (a-1) P + b inc),  P' = P + D'
+//   adjoint  G' = G + inc,  Q' = a Q + b G'  (final step: x = G' + ((a-1)/b) Q)
+// Tiles that do not reach the layer use a = b = 1 without loading the factors.
+template <int R, int MODE, int SP>
 __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
                                                              int* status, long long timeout_ns) {
   using G = G2<R>;
@@ -140,6 +145,18 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       break;
     }
     const float* P = stage0 + s * G::STAGE;
+    // absorbing layer: factors of this thread's cells when the tile reaches the layer
+    const bool layer = SP != 0 && (gx0 < a.sp_w || gx0 + TX > nx - a.sp_w || gy0 < a.sp_w || gy0 + TY > ny - a.sp_w);
+    float4 sa4[RUN], sb4[RUN];
+#pragma unroll
+    for (int rr = 0; rr < RUN; ++rr) {
+      sa4[rr] = sb4[rr] = make_float4(1.f, 1.f, 1.f, 1.f);
+      const int gy = gy0 + r0 + rr;
+      if (SP != 0 && layer && gy < ny && gx < nx) {
+        sa4[rr] = __ldg(reinterpret_cast<const float4*>(a.sp_a + (long long)gy * nx + gx));
+        sb4[rr] = __ldg(reinterpret_cast<const float4*>(a.sp_b + (long long)gy * nx + gx));
+      }
+    }
     if (INJ && inj_e > inj_b) {  // G += S^T r_m in the owners' registers; the shared tile is cleared again
 #pragma unroll
       for (int rr = 0; rr < RUN; ++rr) {
@@ -189,8 +206,18 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
           inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
         else
           inc = fmaf(ckh, acc, ckl * acc);
-        dn[j] = f4get(d4[rr], j) + inc;
-        pn[j] = a.final_step ? dn[j] : c + dn[j];
+        if (SP == 0 || !layer) {
+          dn[j] = f4get(d4[rr], j) + inc;
+          pn[j] = a.final_step ? dn[j] : c + dn[j];
+        } else if (SP == 1) {  // forward in the layer
+          const float fa = f4get(sa4[rr], j), fb = f4get(sb4[rr], j);
+          dn[j] = load_d ? fmaf(fa, f4get(d4[rr], j), fb * inc) : fmaf(fa - 1.f, c, fb * inc);
+          pn[j] = c + dn[j];
+        } else {  // adjoint in the layer
+          const float fa = f4get(sa4[rr], j), fb = f4get(sb4[rr], j);
+          dn[j] = f4get(d4[rr], j) + inc;
+          pn[j] = a.final_step ? fmaf((fa - 1.f) / fb, c, dn[j]) : fmaf(fa, c, fb * dn[j]);
+        }
       }
       if (in) {
         *reinterpret_cast<float4*>(a.next + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
@@ -206,25 +233,31 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
     for (int j = max(0, issued - 2); j < issued; ++j) mbar_wait(&bars[j & 1], (j >> 1) & 1, timeout_ns);
 }
 
-template <int R, int MODE>
+template <int R, int MODE, int SP>
 const void* kfn() {
-  return reinterpret_cast<const void*>(&step2d_tma_kernel<R, MODE>);
+  return reinterpret_cast<const void*>(&step2d_tma_kernel<R, MODE, SP>);
 }
 
-const void* kernel_for(int R, int mode) {
-  switch (R * 4 + mode) {
-    case 4 + 0: return kfn<1, 0>();
-    case 4 + 1: return kfn<1, 1>();
-    case 4 + 2: return kfn<1, 2>();
-    case 12 + 0: return kfn<3, 0>();
-    case 12 + 1: return kfn<3, 1>();
-    case 12 + 2: return kfn<3, 2>();
-    case 20 + 0: return kfn<5, 0>();
-    case 20 + 1: return kfn<5, 1>();
-    case 20 + 2: return kfn<5, 2>();
-    case 28 + 0: return kfn<7, 0>();
-    case 28 + 1: return kfn<7, 1>();
-    case 28 + 2: return kfn<7, 2>();
+template <int R>
+const void* kernel_r(int mode, int sp) {
+  switch (mode * 3 + sp) {
+    case 0: return kfn<R, 0, 0>();
+    case 1: return kfn<R, 0, 1>();
+    case 2: return kfn<R, 0, 2>();
+    case 3: return kfn<R, 1, 0>();
+    case 4: return kfn<R, 1, 1>();
+    case 6: return kfn<R, 2, 0>();
+    case 8: return kfn<R, 2, 2>();
+    default: return nullptr;  // varying-medium adjoint and mismatched layer modes are not instantiated
+  }
+}
+
+const void* kernel_for(int R, int mode, int sp) {
+  switch (R) {
+    case 1: return kernel_r<1>(mode, sp);
+    case 3: return kernel_r<3>(mode, sp);
+    case 5: return kernel_r<5>(mode, sp);
+    case 7: return kernel_r<7>(mode, sp);
     default: return nullptr;
   }
 }
@@ -258,12 +291,12 @@ cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* 
 }
 
 // Persistent grid: as many CTAs as fit on the device, at most one per tile.
-int tma2d_ctas(int nx, int ny, int R, int mode) {
-  static int cached[3][8] = {{0}};
-  int& c = cached[mode][R];
+int tma2d_ctas(int nx, int ny, int R, int mode, int sp) {
+  static int cached[3][3][8] = {{{0}}};
+  int& c = cached[mode][sp][R];
   if (!c) {
     int dev = 0, sms = 148, per = 1;
-    const void* fn = kernel_for(R, mode);
+    const void* fn = kernel_for(R, mode, sp);
     const size_t smem = smem_for(R, mode);
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -280,13 +313,15 @@ int tma2d_ctas(int nx, int ny, int R, int mode) {
   return ntiles < c ? ntiles : c;
 }
 
-long long tma2d_threads(int nx, int ny, int R, int mode) { return (long long)tma2d_ctas(nx, ny, R, mode) * THREADS; }
+long long tma2d_threads(int nx, int ny, int R, int mode, int sp) {
+  return (long long)tma2d_ctas(nx, ny, R, mode, sp) * THREADS;
+}
 
-cudaError_t step2d_tma_launch(int R, int mode, const StepArgs& a, const CUtensorMap& p, int* status,
+cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, int* status,
                               long long timeout_ns, cudaStream_t st) {
-  const void* fn = kernel_for(R, mode);
+  const void* fn = kernel_for(R, mode, sp);
   if (!fn) return cudaErrorInvalidValue;
-  const int nctas = tma2d_ctas(a.nx, a.ny, R, mode);  // sets the kernel's attributes once
+  const int nctas = tma2d_ctas(a.nx, a.ny, R, mode, sp);  // sets the kernel's attributes once
   CUtensorMap map = p;
   StepArgs args = a;
   void* params[] = {&args, &map, &status, &timeout_ns};

@@ -88,26 +88,37 @@ __global__ void __launch_bounds__(S2_THREADS) step2d_kernel(const StepArgs a) {
       const int gx = gx0 + c0 + j, gy = gy0 + r0 + rr;
       if (gx >= nx || gy >= ny) continue;
       const long long gi = (long long)gy * nx + gx;
+      // absorbing layer: factors a, b of the damped update (1 outside the layer)
+      const float fa = a.sp_a ? a.sp_a[gi] : 1.f, fb = a.sp_a ? a.sp_b[gi] : 1.f;
+      const bool layer = fa != 1.f || fb != 1.f;
       if (ADJ) {
         const float g0 = a.dbuf[gi], gl0 = a.dbuf_lo[gi];
-        if (a.final_step) {  // x = S^T r_0 (already in G) + G + 1/2 L(kappa Q^1)
-          a.next[gi] = fmaf(a.c_lap, L[rr][j], g0 + gl0);
+        if (a.final_step) {  // x = S^T r_0 (already in G) + G + 1/2 L(kappa Q^1) [+ ((a-1)/b) Q^1]
+          float xv = fmaf(a.c_lap, L[rr][j], g0 + gl0);
+          if (layer) xv = fmaf((fa - 1.f) / fb, a.cur[gi] + a.cur_lo[gi], xv);
+          a.next[gi] = xv;
           continue;
         }
         float e;
         const float g = two_sum(g0, L[rr][j] + gl0, e);  // G += L(kappa Q)  (compensated)
         a.dbuf[gi] = g;
         a.dbuf_lo[gi] = e;
-        const float q = two_sum(a.cur[gi], g, e);  // Q^n = Q^{n+1} + G  (compensated)
-        a.next[gi] = q;
-        a.next_lo[gi] = a.cur_lo[gi] + e;
+        if (layer) {  // Q^n = a Q^{n+1} + b G (inside the damping layer, compensation carried approximately)
+          a.next[gi] = fmaf(fa, a.cur[gi], fb * g);
+          a.next_lo[gi] = fmaf(fa, a.cur_lo[gi], fb * e);
+        } else {
+          const float q = two_sum(a.cur[gi], g, e);  // Q^n = Q^{n+1} + G  (compensated)
+          a.next[gi] = q;
+          a.next_lo[gi] = a.cur_lo[gi] + e;
+        }
       } else {
         const float kap = VARC ? a.kappa[gi] : a.kappa0;
         const float kap_lo = VARC ? a.kappa_lo[gi] : a.kappa0_lo;
         const float cur = S[(r0 + rr + R) * S2_PITCH + S2_XOFF + c0 + j];
         // (kappa_hi + kappa_lo) L rounded once, before it meets the much larger increment
         const float inc = fmaf(a.c_lap * kap, L[rr][j], (a.c_lap * kap_lo) * L[rr][j]);
-        const float d = (a.d_zero ? 0.f : a.dbuf[gi]) + inc;
+        float d = (a.d_zero ? 0.f : a.dbuf[gi]) + inc;
+        if (layer) d = a.d_zero ? fmaf(fa - 1.f, cur, fb * inc) : fmaf(fa, a.dbuf[gi], fb * inc);
         a.dbuf[gi] = d;
         a.next[gi] = cur + d;
       }

@@ -71,6 +71,11 @@ class Plan:
     def path(self, p):
         _lib.pat_plan_set_path(self.handle, p)
 
+    def set_sponge(self, width, sigma_max=0.0, stream=None):
+        """Absorbing layer of `width` cells (0 removes it); sigma_max 0 selects
+        the nominal-reflection-1e-3 default.  2D plans only."""
+        _lib.pat_plan_set_sponge(self.handle, width, sigma_max, self._stream(stream))
+
     def check(self, stream=None):
         return _lib.pat_plan_check(self.handle, self._stream(stream))
 
