@@ -23,7 +23,8 @@ engine, one step = one batched solve, beside the same solves one after the
 other.
 
 --sweep prints one line per grid of the per-step engines' HBM sweep
-(2D 2048^2 .. 16384^2 x orders {2, 8}, 3D 256^3 and 512^3 order 4).
+(2D 2048^2 .. 16384^2 x orders {2, 8}, 4096^2 order 8 with a varying medium
+and with a 10-cell absorbing layer, 3D 256^3 and 512^3 order 4).
 
 --impl reference runs the FP64 CPU oracle (the reference arm of this
 build): each step is one oracle CG iteration of the same workload (for the
@@ -463,21 +464,24 @@ def run_sweep(args):
     import torch
     from paper_2507_02401_gb300 import Plan
     peak, peak_kind = peaks()
-    cases = [((n, n), o, False) for n in (2048, 4096, 8192, 16384) for o in (2, 8)]
-    cases += [((4096, 4096), 8, True), ((256, 256, 256), 4, False), ((512, 512, 512), 4, False)]
+    cases = [((n, n), o, False, 0) for n in (2048, 4096, 8192, 16384) for o in (2, 8)]
+    cases += [((4096, 4096), 8, True, 0), ((4096, 4096), 8, False, 10), ((256, 256, 256), 4, False, 0),
+              ((512, 512, 512), 4, False, 0)]
     nt = 201
     if args.only:  # a grid ("4096x4096") or one case ("4096x4096-o8", "4096x4096-o8v" for the varying medium)
         def ids(cs):
             g = "x".join(map(str, cs[0]))
-            return {g, f"{g}-o{cs[1]}" + ("v" if cs[2] else "")}
+            return {g, f"{g}-o{cs[1]}" + ("v" if cs[2] else "") + ("s" if cs[3] else "")}
         cases = [cs for cs in cases if args.only in ids(cs)]
-    for shape, order, varc in cases:
+    for shape, order, varc, sponge in cases:
         h = 1e-4
         rng = np.random.default_rng(0)
         c = 1400.0 + 200.0 * rng.random(shape).astype(np.float32) if varc else 1500.0
         dt = 0.3 * h / 1600.0
         sens = np.stack([rng.uniform(0.1, 0.9, 64) * (n - 1) * h for n in shape[::-1]], axis=1)
         plan = Plan(shape, h, dt, nt, order, c, sens, 1, 0)
+        if sponge:
+            plan.set_sponge(sponge)  # absorbing layer, default damping rate
         x = torch.randn(shape, device="cuda")
         y = torch.empty((64, nt), device="cuda")
         xa = torch.empty(shape, device="cuda")
@@ -496,6 +500,7 @@ def run_sweep(args):
         N = int(np.prod(shape))
         bpp = 16 if varc else 12
         line = {"sweep": "x".join(map(str, shape)), "order": order, "medium": "varying" if varc else "constant",
+                "absorbing_layer_cells": sponge,
                 "engine": {1: "persistent", 2: "step"}.get(plan.path, "?"), "steps": nt - 1,
                 "algorithmic_bytes_per_point_update": bpp, "peak_gbs": peak, "peak_kind": peak_kind}
         for name in ("K", "Kt"):
