@@ -149,6 +149,37 @@ pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int
                      float* x, double* log, void* stream);
 
 /*
+ * pat_solve_gmres — the paper's solver (Sec. 4 and 5: GMRES, 15 iterations
+ * = 31 wave evaluations in its experiments) on the image-space system of
+ * Eq. linear_minimization with the covariance Gamma = E_s E_s*:
+ *   (Gamma K* K + alpha I) x = Gamma K* y,   x_0 = 0.
+ * Arnoldi with modified Gram-Schmidt (FP32 basis vectors, FP64 inner
+ * products reduced in a fixed order), Givens rotations and the Hessenberg
+ * matrix on the host in FP64.  Converges to the same minimiser as pat_solve
+ * (x = E_s u).  Synchronous; allocates the (iters+1) x N basis per call.
+ *   x    N floats (output; device or host).
+ *   res  NULL or HOST array of iters+1 doubles: ||f - A x_k|| for k = 0..iters.
+ *   J    NULL or HOST array of iters+1 doubles: J(u_k) = 1/2 ||K x_k - y||^2
+ *        + alpha/2 ||u_k||^2 with u_k = E_s^{-1} x_k (costs one extra K per
+ *        iteration).
+ * Errors: PAT_ERR_INVALID (arguments), PAT_ERR_OOM (basis), PAT_ERR_CUDA.
+ */
+pat_status pat_solve_gmres(pat_plan* plan, const float* y, double alpha, double s, int iters, float* x, double* res,
+                           double* J, void* stream);
+
+/*
+ * pat_solve_landweber — the Landweber (gradient) iteration on the coefficient
+ * system: u_{k+1} = u_k - omega ((E_s* K* K E_s + alpha I) u_k - E_s* K* y),
+ * u_0 = 0; it converges for 0 < omega < 2 / lambda_max.  Synchronous.
+ *   u, x  N floats (outputs, may be NULL): final coefficients and image E_s u.
+ *   J     NULL or HOST array of iters+1 doubles: J(u_k) for k = 0..iters
+ *         (the forward map of each iterate is computed anyway; the last value
+ *         costs one extra K).
+ */
+pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, double s, int iters, double omega,
+                               float* u, float* x, double* J, void* stream);
+
+/*
  * pat_solve_batched — B independent pat_solve problems (each with its own
  * plan, data, alpha and s; a common iteration count) advanced together.
  * When every plan qualifies for a batch (see pat_batch_create) and ys / xs

@@ -42,6 +42,10 @@ SIGNATURES = [
     ("pat_EsT", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("pat_solve", c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p]),
+    ("pat_solve_gmres", c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p,
+                                c_void_p]),
+    ("pat_solve_landweber", c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, c_void_p, c_void_p,
+                                    c_void_p, c_void_p]),
     ("pat_solve_batched", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p]),
     ("pat_batch_create", c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
@@ -164,6 +168,17 @@ def pat_EsT(plan, s, x, u, stream=None):
 def pat_solve(plan, y, alpha, s, iters, u0, u, x, log=None, stream=None):
     return _check(load().pat_solve(plan, ptr(y), float(alpha), float(s), int(iters), ptr(u0), ptr(u), ptr(x),
                                    ptr(log), stream_handle(stream)))
+
+
+def pat_solve_gmres(plan, y, alpha, s, iters, x, res=None, J=None, stream=None):
+    """res, J: None or float64 numpy arrays of iters+1 values (host)."""
+    return _check(load().pat_solve_gmres(plan, ptr(y), float(alpha), float(s), int(iters), ptr(x), ptr(res), ptr(J),
+                                         stream_handle(stream)))
+
+
+def pat_solve_landweber(plan, y, alpha, s, iters, omega, u=None, x=None, J=None, stream=None):
+    return _check(load().pat_solve_landweber(plan, ptr(y), float(alpha), float(s), int(iters), float(omega), ptr(u),
+                                             ptr(x), ptr(J), stream_handle(stream)))
 
 
 def pat_solve_batched(plans, ys, alphas, ss, iters, xs, stream=None):

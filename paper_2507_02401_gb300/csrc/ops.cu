@@ -804,6 +804,48 @@ pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int
   return PAT_OK;
 }
 
+pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, double s, int iters, double omega,
+                               float* u, float* x, double* J, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!y || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(s) || iters < 0 || !(omega > 0.0) ||
+      !std::isfinite(omega)) {
+    set_error("y must not be NULL, alpha and omega finite and > 0, s finite, iters >= 0");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float* dy;
+  float *du, *dx;
+  bool hy, hu, hx;
+  PAT_TRY(in_arr(plan, 0, y, ny, &dy, &hy, st));
+  PAT_TRY(out_arr(plan, 2, u, plan->N, &du, &hu));
+  PAT_TRY(out_arr(plan, 3, x, plan->N, &dx, &hx));
+  PAT_TRY(landweber_device(plan, dy, alpha, s, iters, omega, du, dx, J, st));
+  if (u) PAT_TRY(out_back(u, du, plan->N, hu, st));
+  if (x) PAT_TRY(out_back(x, dx, plan->N, hx, st));
+  PAT_TRY_CUDA(cudaStreamSynchronize(st));
+  return PAT_OK;
+}
+
+pat_status pat_solve_gmres(pat_plan* plan, const float* y, double alpha, double s, int iters, float* x, double* res,
+                           double* J, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!y || !x || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(s) || iters < 0) {
+    set_error("y and x must not be NULL, alpha finite and > 0, s finite, iters >= 0");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float* dy;
+  float* dx;
+  bool hy, hx;
+  PAT_TRY(in_arr(plan, 0, y, ny, &dy, &hy, st));
+  PAT_TRY(out_arr(plan, 3, x, plan->N, &dx, &hx));
+  PAT_TRY(gmres_device(plan, dy, alpha, s, iters, dx, res, J, st));
+  PAT_TRY(out_back(x, dx, plan->N, hx, st));
+  return PAT_OK;
+}
+
 pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* ys, const double* alphas,
                              const double* ss, int iters, float* const* xs, pat_status* per_inst, void* stream) {
   if (B < 0 || (B > 0 && (!plans || !ys || !alphas || !ss || !xs))) {

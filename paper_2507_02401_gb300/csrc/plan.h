@@ -81,6 +81,7 @@ struct pat_plan {
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   int* d_status = nullptr;
+  double* d_kr = nullptr;  // GMRES / Landweber reduction partials (allocated on first use)
 
   // ---- staging for host arrays
   float* d_stage[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -112,4 +113,8 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
 pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int iters, const float* u0, float* u,
                         float* x, double* log, cudaStream_t st);
 pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float* g, int segment, cudaStream_t st);
+pat_status landweber_device(pat_plan* p, const float* y, double alpha, double s, int iters, double omega, float* u,
+                            float* x, double* J, cudaStream_t st);
+pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int iters, float* x, double* res,
+                        double* J, cudaStream_t st);
 }  // namespace pat

@@ -125,6 +125,26 @@ class Plan:
         return u, x, (log[:iters] if want_log else None)
 
 
+    def solve_gmres(self, y, alpha, s, iters, want_log=False, stream=None):
+        """GMRES on the paper's image-space system; returns (x, res, J) with
+        res and J numpy arrays of iters+1 values (None unless want_log)."""
+        y = self._f32(y)
+        x = torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        res = np.zeros(iters + 1) if want_log else None
+        J = np.zeros(iters + 1) if want_log else None
+        _lib.pat_solve_gmres(self.handle, y, alpha, s, iters, x, res, J, self._stream(stream))
+        return x, res, J
+
+    def solve_landweber(self, y, alpha, s, iters, omega, want_log=False, stream=None):
+        """Landweber iteration; returns (u, x, J) (J: numpy, iters+1 values, or None)."""
+        y = self._f32(y)
+        u = torch.empty(self.N, device="cuda", dtype=torch.float32)
+        x = torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        J = np.zeros(iters + 1) if want_log else None
+        _lib.pat_solve_landweber(self.handle, y, alpha, s, iters, omega, u, x, J, self._stream(stream))
+        return u, x, J
+
+
 class Batch:
     """Many 2D constant-medium plans advanced together by the batched engine
     (one launch per time step over all instances' tiles; tile height chosen
