@@ -22,6 +22,10 @@ iterations per step).
 engine, one step = one batched solve, beside the same solves one after the
 other.
 
+--workload limited times the paper-like limited-view experiment: 512x512
+with a 10-cell absorbing layer, 80 sensors along one face, data simulated
+on a grid twice as fine, one step = one 15-iteration GMRES reconstruction.
+
 --sweep prints one line per grid of the per-step engines' HBM sweep
 (2D 2048^2 .. 16384^2 x orders {2, 8}, 4096^2 order 8 with a varying medium
 and with a 10-cell absorbing layer, 3D 256^3 and 512^3 order 4).
@@ -69,6 +73,16 @@ WORKLOADS = {
         "profile": "step3d_tma_256_o4.txt",
         "sources": ("wave3d_tma.cu", "stencil.cuh", "tma.cuh"),
         "oracle_nt": 40,  # oracle samples: one K + K* pair at 40 steps, scaled linearly to 800
+    },
+    "limited": {
+        "desc": ("2D 512x512 limited view: c = 1500 m/s, 10-cell absorbing layer, 80 sensors in a row inside one "
+                 "face, order-8 staggered FDTD, 2414 steps, data simulated on a 1024x1024 grid at half the time "
+                 "step and sampled at every second step (no inverse crime), 2% noise, db4 5 levels, s = 1, "
+                 "alpha = 1e-2 (relative), 15 GMRES iterations on the paper's image-space system"),
+        "kernel": "step2d_tma_kernel<R=7> with the absorbing layer",
+        "profile": "step2d_tma_4096_o8.txt",
+        "sources": ("wave2d_tma.cu", "stencil.cuh", "tma.cuh"),
+        "oracle_nt": 40,
     },
 }
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]["desc"]
@@ -515,6 +529,116 @@ def run_sweep(args):
     return 0
 
 
+def run_limited(args):
+    """Limited-view workload: one step = one 15-iteration GMRES reconstruction
+    (the paper's solver) with the absorbing layer, from data simulated on a
+    grid twice as fine; also reports the relative error of the GMRES image for
+    s in {0, 0.5, 1, 1.5, 2} and the objective J per iterate at s = 1."""
+    import torch
+
+    import synth
+    from paper_2507_02401_gb300 import Plan, _lib
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    rank, world, local = dist_setup(True)
+    spec = WORKLOADS["limited"]
+    w = synth.workload("limited", seed=1005 + rank)
+    ex = w.extra
+    iters = args.iters or w.iters
+    nf = w.shape[0] * ex["refine"]
+    fine = Plan((nf, nf), ex["h_fine"], ex["dt_fine"], ex["nt_fine"], w.order, 1500.0, w.sensors, 1, 0)
+    fine.set_sponge(ex["layer"] * ex["refine"])
+    y_f = fine.forward(torch.as_tensor(ex["x_fine"], dtype=torch.float32, device="cuda")).cpu().numpy()
+    fine.close()
+    y_np = synth.add_noise(y_f[:, ::ex["refine"]].astype(np.float64), w.noise,
+                           np.random.default_rng(1234 + rank)).astype(np.float32)
+    plan = Plan(w.shape, w.h, w.dt, w.nt, w.order, 1500.0, w.sensors, w.family, w.levels)
+    plan.set_sponge(ex["layer"])
+    y = torch.as_tensor(y_np, device="cuda")
+    s1 = 1.0
+    alpha = w.alpha[0] * lambda_max(plan, s1, iters=args.power_iters)
+    stream = torch.cuda.current_stream()
+    x = torch.empty(w.shape, device="cuda")
+
+    def solve():
+        _lib.pat_solve_gmres(plan.handle, y, alpha, s1, iters, x, None, None, stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    _lib.pat_plan_profile(plan.handle, 1)
+    sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        solve()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, True)
+    kernels, wave_calls, wave_ms, points = _lib.pat_plan_profile_read(plan.handle)
+    _lib.pat_plan_profile(plan.handle, 0)
+    # end to end through the C ABI with host arrays
+    x_host = np.zeros(w.shape, dtype=np.float32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _lib.pat_solve_gmres(plan.handle, y_np, alpha, s1, iters, x_host, None, None, stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, True)
+    # reconstruction quality (outside the timed region)
+    errs = {}
+    xt = w.x_true
+    for s in w.s:
+        a_s = w.alpha[0] * lambda_max(plan, s, iters=args.power_iters)
+        xs, res, J = plan.solve_gmres(y, a_s, s, iters, want_log=(s == s1))
+        errs[str(s)] = float(np.linalg.norm(xs.cpu().numpy() - xt) / np.linalg.norm(xt))
+        if s == s1:
+            J_curve, res_curve = [float(v) for v in J], [float(v) for v in res]
+    # algorithmic bytes of the step kernel per time step (12 B per point-update, constant medium)
+    launches = wave_calls * (w.nt - 1)
+    launch_ms = wave_ms / max(launches, 1)
+    achieved = 12.0 * w.N / (launch_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
+    peak, peak_kind = peaks()
+    # GMRES vector kernels besides the library's counted wave and wavelet kernels, per solve
+    extra = 4 + sum(1 + 3 * (j + 1) + 3 for j in range(iters)) + 1 + iters
+    line = {
+        "metric": METRIC, "value": world * args.steps * iters / (t_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec["desc"], "engine": "step", "solver": "GMRES", "iters_per_step": iters,
+                   "l2": "256 MiB buffer written before every step (inside the timed region)",
+                   "parallelism": f"replicas x{world} (independent instances per rank)"},
+        "rel_error_by_s": errs, "J_per_iterate_s1": J_curve, "residual_per_iterate_s1": res_curve,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": spec["kernel"],
+                     "algorithmic_bytes_per_point_update": 12, "launch_ms": launch_ms, "launches_timed": launches,
+                     "launch": "one time step (averaged over whole K / K* applications, injection included)",
+                     "note": "512^2 fields are L2-resident"},
+        "e2e": {"value": world * args.steps * iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_np.nbytes),
+                "d2h_bytes_per_step": int(w.N * 4)},
+        "gpu_launches": int(kernels + args.steps * (extra + 1)),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_iters, "limited")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
 def run_batch(args):
     """64 independent reconstructions of uneven size through the batched
     engine (one step = one 50-iteration batched solve of all instances),
@@ -683,6 +807,8 @@ def main():
         return run_sweep(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "limited":
+        return run_limited(args)
     return run_ours(args)
 
 

@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -145,18 +146,8 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       break;
     }
     const float* P = stage0 + s * G::STAGE;
-    // absorbing layer: factors of this thread's cells when the tile reaches the layer
+    // absorbing layer: does the tile reach it (its factors are then loaded row by row)
     const bool layer = SP != 0 && (gx0 < a.sp_w || gx0 + TX > nx - a.sp_w || gy0 < a.sp_w || gy0 + TY > ny - a.sp_w);
-    float4 sa4[RUN], sb4[RUN];
-#pragma unroll
-    for (int rr = 0; rr < RUN; ++rr) {
-      sa4[rr] = sb4[rr] = make_float4(1.f, 1.f, 1.f, 1.f);
-      const int gy = gy0 + r0 + rr;
-      if (SP != 0 && layer && gy < ny && gx < nx) {
-        sa4[rr] = __ldg(reinterpret_cast<const float4*>(a.sp_a + (long long)gy * nx + gx));
-        sb4[rr] = __ldg(reinterpret_cast<const float4*>(a.sp_b + (long long)gy * nx + gx));
-      }
-    }
     if (INJ && inj_e > inj_b) {  // G += S^T r_m in the owners' registers; the shared tile is cleared again
 #pragma unroll
       for (int rr = 0; rr < RUN; ++rr) {
@@ -170,62 +161,76 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       }
     }
 
-    // sliding window over this thread's 4 columns: win[i] = box row (row - R + i)
-    float4 win[2 * R + 1];
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(P + (r0 + i) * BW + XH + c0);
-#pragma unroll
-    for (int rr = 0; rr < RUN; ++rr) {
-      win[2 * R] = *reinterpret_cast<const float4*>(P + (r0 + rr + 2 * R) * BW + XH + c0);
-      const int brow = r0 + rr + R;
-      float f[20];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const float4 v = *reinterpret_cast<const float4*>(P + brow * BW + c0 + 4 * q);
-        f[4 * q + 0] = v.x;
-        f[4 * q + 1] = v.y;
-        f[4 * q + 2] = v.z;
-        f[4 * q + 3] = v.w;
-      }
-      const int gy = gy0 + r0 + rr;
-      const long long gi = (long long)gy * nx + gx;
-      const bool in = gy < ny && gx < nx;
-      float dn[4], pn[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float c = f[8 + j];
-        const float c2 = c + c;
-        float acc = 0.f;  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
-#pragma unroll
-        for (int m = 1; m <= R; ++m)
-          acc = fmaf(a.w[m], pair_term<false>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
-#pragma unroll
-        for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<false>(f[8 + j + m], f[8 + j - m], c, c2), acc);
-        float inc;
-        if (VARC)
-          inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
-        else
-          inc = fmaf(ckh, acc, ckl * acc);
-        if (SP == 0 || !layer) {
-          dn[j] = f4get(d4[rr], j) + inc;
-          pn[j] = a.final_step ? dn[j] : c + dn[j];
-        } else if (SP == 1) {  // forward in the layer
-          const float fa = f4get(sa4[rr], j), fb = f4get(sb4[rr], j);
-          dn[j] = load_d ? fmaf(fa, f4get(d4[rr], j), fb * inc) : fmaf(fa - 1.f, c, fb * inc);
-          pn[j] = c + dn[j];
-        } else {  // adjoint in the layer
-          const float fa = f4get(sa4[rr], j), fb = f4get(sb4[rr], j);
-          dn[j] = f4get(d4[rr], j) + inc;
-          pn[j] = a.final_step ? fmaf((fa - 1.f) / fb, c, dn[j]) : fmaf(fa, c, fb * dn[j]);
+    // the tile's update; instantiated separately for tiles inside and outside the layer, so that
+    // tiles outside it run exactly the code of the kernel without a layer
+    auto update = [&](auto in_layer) {
+      constexpr bool LAYER = decltype(in_layer)::value;
+      // sliding window over this thread's 4 columns: win[i] = box row (row - R + i)
+      float4 win[2 * R + 1];
+  #pragma unroll
+      for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(P + (r0 + i) * BW + XH + c0);
+  #pragma unroll
+      for (int rr = 0; rr < RUN; ++rr) {
+        win[2 * R] = *reinterpret_cast<const float4*>(P + (r0 + rr + 2 * R) * BW + XH + c0);
+        const int brow = r0 + rr + R;
+        float f[20];
+  #pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(P + brow * BW + c0 + 4 * q);
+          f[4 * q + 0] = v.x;
+          f[4 * q + 1] = v.y;
+          f[4 * q + 2] = v.z;
+          f[4 * q + 3] = v.w;
         }
+        const int gy = gy0 + r0 + rr;
+        const long long gi = (long long)gy * nx + gx;
+        const bool in = gy < ny && gx < nx;
+        float dn[4], pn[4];
+        float4 sa4 = make_float4(1.f, 1.f, 1.f, 1.f), sb4 = sa4;
+        if (LAYER && in) {
+          sa4 = __ldg(reinterpret_cast<const float4*>(a.sp_a + gi));
+          sb4 = __ldg(reinterpret_cast<const float4*>(a.sp_b + gi));
+        }
+  #pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float c = f[8 + j];
+          const float c2 = c + c;
+          float acc = 0.f;  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
+  #pragma unroll
+          for (int m = 1; m <= R; ++m)
+            acc = fmaf(a.w[m], pair_term<false>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
+  #pragma unroll
+          for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<false>(f[8 + j + m], f[8 + j - m], c, c2), acc);
+          float inc;
+          if (VARC)
+            inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
+          else
+            inc = fmaf(ckh, acc, ckl * acc);
+          if (!LAYER) {
+            dn[j] = f4get(d4[rr], j) + inc;
+            pn[j] = a.final_step ? dn[j] : c + dn[j];
+          } else if (SP == 1) {  // forward in the layer
+            const float fa = f4get(sa4, j), fb = f4get(sb4, j);
+            dn[j] = load_d ? fmaf(fa, f4get(d4[rr], j), fb * inc) : fmaf(fa - 1.f, c, fb * inc);
+            pn[j] = c + dn[j];
+          } else {  // adjoint in the layer
+            const float fa = f4get(sa4, j), fb = f4get(sb4, j);
+            dn[j] = f4get(d4[rr], j) + inc;
+            pn[j] = a.final_step ? fmaf((fa - 1.f) / fb, c, dn[j]) : fmaf(fa, c, fb * dn[j]);
+          }
+        }
+        if (in) {
+          *reinterpret_cast<float4*>(a.next + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+          if (!a.final_step) *reinterpret_cast<float4*>(a.dbuf + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+        }
+  #pragma unroll
+        for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
       }
-      if (in) {
-        *reinterpret_cast<float4*>(a.next + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-        if (!a.final_step) *reinterpret_cast<float4*>(a.dbuf + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
-    }
+    };
+    if (SP != 0 && layer)
+      update(std::true_type{});
+    else
+      update(std::false_type{});
     __syncthreads();  // this stage is refilled by the next iteration's TMA
   }
   // after a timed-out wait: give the copies in flight a bounded chance to land

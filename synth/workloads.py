@@ -98,6 +98,39 @@ def arc_2d(n=1024, nt=3000, order=8, ns=256, levels=6, seed=1002, iters=100):
                     sensors.arc(n, H, ns), 4, levels, [1.5], [1e-2], iters, 0.01, x, seed)
 
 
+def limited_view(n=512, sides=1, ns=80, order=8, levels=5, seed=1005, iters=15, layer=10, refine=2):
+    """The paper's experiment in synthetic form: n x n, c = 1500 m/s, an
+    absorbing layer of `layer` cells, `ns` point sensors on one side (sides=1:
+    a row `layer`+1 cells inside the top face) or split over two adjacent sides
+    (sides=2: the top row and the left column), p0 = 4 blobs + 6 Bezier
+    vessels, 2% noise, db4, s in {0, 0.5, 1, 1.5, 2}, 15 iterations, alpha
+    1e-2 (relative).  Against the inverse crime the data are to be simulated
+    on a grid `refine` times finer (spacing h/refine, time step dt/refine,
+    the same sensor positions) and sampled at every `refine`-th time step;
+    the fine-grid phantom is extra["x_fine"] and x_true is its refine x refine
+    block mean.  nt covers the grid diagonal at CFL 0.3."""
+    rng = np.random.default_rng(seed)
+    nf = n * refine
+    xf = phantoms.blobs((nf, nf), 4, rng, sigma=(2.0 * refine, 6.0 * refine)) + phantoms.vessels2d(
+        (nf, nf), 6, rng, width=tuple(w * refine for w in (1, 2, 3)))
+    x = xf.reshape(n, refine, n, refine).mean(axis=(1, 3))
+    d = (layer + 1) * H
+    lo, hi = (layer + 4) * H, (n - layer - 5) * H
+    if sides == 1:
+        pos = np.stack([np.linspace(lo, hi, ns), np.full(ns, d)], axis=1)
+    else:
+        a = ns // 2
+        top = np.stack([np.linspace(lo, hi, a), np.full(a, d)], axis=1)
+        left = np.stack([np.full(ns - a, d), np.linspace(lo, hi, ns - a)], axis=1)
+        pos = np.concatenate([top, left])
+    nt = int(ceil(sqrt(2.0) * n / CFL))
+    w = Workload("2d-%d-o%d-limited%d" % (n, order, sides), (n, n), H, 1500.0, _dt(H, 1500.0), nt, order, pos, 4,
+                 levels, [0.0, 0.5, 1.0, 1.5, 2.0], [1e-2], iters, 0.02, x, seed)
+    w.extra.update(x_fine=xf, refine=refine, layer=layer, h_fine=H / refine, dt_fine=_dt(H, 1500.0) / refine,
+                   nt_fine=refine * (nt - 1) + 1)
+    return w
+
+
 def tree_3d(n=256, nt=800, order=4, ns=4096, levels=4, seed=1004, iters=30):
     """3D grid, constant c, sensors on a Fibonacci sphere, p0 = vessel tree +
     5 blobs, 1% noise, 3D db4, s = 1, alpha = 1e-2."""
@@ -134,6 +167,7 @@ WORKLOADS = {
     "vessels": vessels_2d,
     "arc": arc_2d,
     "tree3d": tree_3d,
+    "limited": limited_view,
 }
 
 
