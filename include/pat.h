@@ -280,6 +280,21 @@ pat_status pat_plan_set_path(pat_plan* plan, int path);
 pat_status pat_plan_get_path(const pat_plan* plan, int* path);
 
 /*
+ * pat_plan_set_prior — choose the form of E_s.  kind 0: the periodic
+ * Daubechies wavelet form (the default, Prop. 4.2).  kind 1: the Fourier
+ * form of Sec. 4 (implementation), where the paper applies its adjoint
+ * embedding as ifft(B . fft(X)) with the Bessel potential
+ * B = (1 + 4 pi^2 |xi|^2)^{-s}; that operator is this library's covariance
+ * E_s E_s*, so E_s (= E_s*) is the filter with (1 + 4 pi^2 |xi|^2)^{-s/2}.
+ * Lengths are measured in units of `length_cells` cells: DFT index k of an
+ * n-cell axis is xi = k' length_cells / n, k' = k (k < n/2) or k - n.
+ * Coefficients then live on the grid (N values, no wavelet bands).  Requires
+ * a 2D grid with power-of-two extents up to 4096 (PAT_ERR_INVALID
+ * otherwise).  Allocates two complex N-buffers on first use.
+ */
+pat_status pat_plan_set_prior(pat_plan* plan, int kind, double length_cells, void* stream);
+
+/*
  * pat_plan_set_sponge — absorbing layer of `width` cells along every face of
  * a 2D grid (width = 0 removes it).  The paper's simulations absorb outgoing
  * waves with a perfectly matched layer of 10 grid points (Sec. 5); this

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("pat_plan_get_path", c_int, [c_void_p, ctypes.POINTER(c_int)]),
     ("pat_plan_set_timeout", c_int, [c_void_p, c_longlong]),
     ("pat_plan_set_sponge", c_int, [c_void_p, c_int, c_double, c_void_p]),
+    ("pat_plan_set_prior", c_int, [c_void_p, c_int, c_double, c_void_p]),
     ("pat_plan_profile", c_int, [c_void_p, c_int]),
     ("pat_plan_profile_read", c_int, [c_void_p, ctypes.POINTER(c_longlong), ctypes.POINTER(c_int),
                                       ctypes.POINTER(c_double), ctypes.POINTER(c_longlong)]),
@@ -255,6 +256,10 @@ def pat_plan_get_path(plan):
 
 def pat_plan_set_sponge(plan, width, sigma_max=0.0, stream=None):
     return _check(load().pat_plan_set_sponge(plan, int(width), float(sigma_max), stream_handle(stream)))
+
+
+def pat_plan_set_prior(plan, kind, length_cells=1.0, stream=None):
+    return _check(load().pat_plan_set_prior(plan, int(kind), float(length_cells), stream_handle(stream)))
 
 
 def pat_plan_set_timeout(plan, timeout_ns):

@@ -341,6 +341,10 @@ static long long band_offset(const pat_plan* p, int i, int b) {
 }
 
 pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream_t st) {
+  if (p->prior == 1) {  // Fourier form: E_s* = E_s
+    count_kernels(p, 5);
+    return fourier_apply(p, s, x, u, st);
+  }
   const int m = p->levels;
   if (m == 0) {  // no levels: W = I, the coefficients are the image
     if (u != x) PAT_TRY_CUDA(cudaMemcpyAsync(u, x, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, st));
@@ -377,6 +381,10 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
 }
 
 pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_t st) {
+  if (p->prior == 1) {
+    count_kernels(p, 5);
+    return fourier_apply(p, s, u, x, st);
+  }
   const int m = p->levels;
   if (m == 0) {
     if (u != x) PAT_TRY_CUDA(cudaMemcpyAsync(x, u, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, st));

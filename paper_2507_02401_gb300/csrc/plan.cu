@@ -588,6 +588,28 @@ pat_status pat_plan_set_path(pat_plan* plan, int path) {
   return PAT_OK;
 }
 
+pat_status pat_plan_set_prior(pat_plan* plan, int kind, double length_cells, void* stream) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return PAT_ERR_INVALID;
+  }
+  if (kind == 0) {
+    plan->prior = 0;
+    return PAT_OK;
+  }
+  if (kind != 1 || !std::isfinite(length_cells) || !(length_cells > 0.0)) {
+    set_error("prior kind must be 0 (wavelet) or 1 (Fourier) with length_cells finite and > 0");
+    return PAT_ERR_INVALID;
+  }
+  if (!fourier_supported(plan->dim, plan->n[0], plan->n[1])) {
+    set_error("the Fourier prior needs a 2D grid with power-of-two extents up to 4096");
+    return PAT_ERR_INVALID;
+  }
+  PAT_TRY(fourier_setup(plan, length_cells, (cudaStream_t)stream));
+  plan->prior = 1;
+  return PAT_OK;
+}
+
 pat_status pat_plan_set_sponge(pat_plan* plan, int width, double sigma_max, void* stream) {
   if (!plan) {
     set_error("plan is NULL");

@@ -69,6 +69,12 @@ struct pat_plan {
   };
   std::vector<TmaDesc> tma_desc;  // descriptors by field address (small, most recent last)
 
+  // ---- Fourier-form prior (kind 1 of pat_plan_set_prior): lengths in units of fourier_lc cells
+  int prior = 0;
+  double fourier_lc = 1.0;
+  float2* d_fc = nullptr;  // two complex N-buffers (spectrum and its transpose)
+  float2* d_tw = nullptr;  // twiddle tables of the x and y transforms
+
   // ---- wavelet scratch
   float* d_dwt_a = nullptr;  // approximation ping-pong (2 x N/2^dim)
   float* d_dwt_b = nullptr;
@@ -113,6 +119,9 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
 pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int iters, const float* u0, float* u,
                         float* x, double* log, cudaStream_t st);
 pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float* g, int segment, cudaStream_t st);
+bool fourier_supported(int dim, int nx, int ny);
+pat_status fourier_setup(pat_plan* p, double length_cells, cudaStream_t st);
+pat_status fourier_apply(pat_plan* p, double s, const float* in, float* out, cudaStream_t st);
 pat_status landweber_device(pat_plan* p, const float* y, double alpha, double s, int iters, double omega, float* u,
                             float* x, double* J, cudaStream_t st);
 pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int iters, float* x, double* res,

@@ -71,6 +71,11 @@ class Plan:
     def path(self, p):
         _lib.pat_plan_set_path(self.handle, p)
 
+    def set_prior(self, kind, length_cells=1.0, stream=None):
+        """kind 0: wavelet form of E_s (default); 1: Fourier form with lengths in
+        units of `length_cells` cells (2D, power-of-two extents)."""
+        _lib.pat_plan_set_prior(self.handle, kind, length_cells, self._stream(stream))
+
     def set_sponge(self, width, sigma_max=0.0, stream=None):
         """Absorbing layer of `width` cells (0 removes it); sigma_max 0 selects
         the nominal-reflection-1e-3 default.  2D plans only."""
