@@ -781,6 +781,41 @@ def run_batch(args):
     return 0
 
 
+def run_prior_sweep(args):
+    """E_s of the two prior forms on 2D grids: the db4 wavelet form (5 levels,
+    fused level kernels) and the Fourier form (radix-2 FFT kernels), time per
+    application (CUDA events, E_s and E_s* alternating) and GB/s against the
+    algorithmic 8 B per pixel (read the input, write the output once)."""
+    import torch
+    from paper_2507_02401_gb300 import Plan
+    peak, peak_kind = peaks()
+    for n in (512, 2048, 4096):
+        h = 1e-4
+        plan = Plan((n, n), h, 0.3 * h / 1500.0, 2, 2, 1500.0, np.zeros((0, 2)), 4, 5)
+        u = torch.randn(n * n, device="cuda")
+        x = torch.empty((n, n), device="cuda")
+        for kind in (0, 1):
+            plan.set_prior(kind, 8.0)
+            for _ in range(args.warmup):
+                plan.Es(u, 1.0, out=x)
+                plan.EsT(x, 1.0, out=u)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(args.steps, 10)
+            ev0.record()
+            for _ in range(reps):
+                plan.Es(u, 1.0, out=x)
+                plan.EsT(x, 1.0, out=u)
+            ev1.record()
+            torch.cuda.synchronize()
+            us = ev0.elapsed_time(ev1) * 1e3 / (2 * reps)
+            gbs = 8.0 * n * n / us / 1e3
+            print(json.dumps({"prior": "wavelet db4 5 levels" if kind == 0 else "Fourier (FFT)", "grid": f"{n}x{n}",
+                              "us_per_application": round(us, 2), "algorithmic_gbs": round(gbs, 1),
+                              "frac": round(gbs / peak, 3), "peak_kind": peak_kind}), flush=True)
+        plan.close()
+    return 0
+
+
 def plan_varc(w):
     return np.ndim(w.c) != 0 and float(np.max(w.c)) != float(np.min(w.c))
 
@@ -797,6 +832,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--power-iters", type=int, default=20, help="power iterations for lambda_max")
     ap.add_argument("--only", default="", help="with --sweep: run only a grid (256x256x256) or a case (4096x4096-o8)")
+    ap.add_argument("--prior-sweep", action="store_true",
+                    help="time E_s of the wavelet and Fourier prior forms on 2D grids instead")
     ap.add_argument("--sweep", action="store_true",
                     help="time the per-step wave engines on 2D 2048^2..16384^2 (orders 2, 8) and 3D grids instead")
     args = ap.parse_args()
@@ -805,6 +842,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.prior_sweep:
+        return run_prior_sweep(args)
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "limited":
