@@ -202,6 +202,11 @@ def max_over_ranks(v, world, use_cuda):
     return float(t.item())
 
 
+def job_throughput(units_per_rank, world, t_ms_max):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (t_ms_max / 1e3)
+
+
 def gpu_index(local):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -425,7 +430,7 @@ def run_ours(args):
     barrier(world)
 
     iters_total = world * args.steps * w.iters
-    value = iters_total / (t_ms / 1e3)
+    value = job_throughput(args.steps * w.iters, world, t_ms)
     bytes_per_pt = 16 if plan_varc(w) else 12
     # the persistent engine runs a whole K or K* per launch, the step engines one time step
     steps_per_launch = (w.nt - 1) if plan.path == 1 else 1
