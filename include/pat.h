@@ -307,8 +307,8 @@ pat_status pat_plan_set_prior(pat_plan* plan, int kind, double length_cells, voi
  * face (d = cells to that face), summed over the two axes.
  *   sigma_max  damping rate at the faces [1/s]; 0 selects
  *              3 c_max ln(1e3) / (2 width h) (nominal reflection 1e-3).
- * The persistent engine has no layer: while one is set the plan runs the
- * per-step engine; the medium gradient and batches reject such plans.
+ * Both 2D engines (persistent and per-step) carry the layer; the medium
+ * gradient and batches reject plans with one.
  * Errors: PAT_ERR_INVALID for 3D plans, width < 0, 2 width > nx or ny, or a
  * negative / non-finite sigma_max.  Synchronises `stream`.
  */

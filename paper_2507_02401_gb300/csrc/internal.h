@@ -80,6 +80,8 @@ struct Persist2DArgs {
   int* status;           // sticky plan status
   long long timeout_ns;  // bound on any single wait
   int poll_ns;           // back-off between polls of the exchange (0 = spin)
+  const float* sp_a;     // absorbing layer: per-cell factors a, b of the damped update (nullptr = none)
+  const float* sp_b;
 };
 
 // Arguments of the per-step kernels.
@@ -138,6 +140,8 @@ size_t persist2d_smem_bytes(int R, bool adj);
 size_t persist2d_xbuf_words(int R, bool adj, int ntiles);  // 64-bit exchange words
 int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
+// the same with the absorbing layer (a.sp_a, a.sp_b set)
+cudaError_t persist2d_launch_layer(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
 cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, int nsplit, int nt, float* y,
                                     cudaStream_t st);
 

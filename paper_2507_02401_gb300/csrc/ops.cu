@@ -32,6 +32,10 @@ static Persist2DArgs persist_args(pat_plan* p) {
   a.status = p->d_status;
   a.timeout_ns = p->timeout_ns;
   a.poll_ns = p->poll_ns;
+  if (p->sponge_w > 0) {
+    a.sp_a = p->d_sp_a;
+    a.sp_b = p->d_sp_b;
+  }
   return a;
 }
 
@@ -40,7 +44,10 @@ static Persist2DArgs persist_args(pat_plan* p) {
 static pat_status persist_launch(pat_plan* p, bool adj, const Persist2DArgs& a, cudaStream_t st) {
   PAT_TRY_CUDA(cudaMemsetAsync(p->d_xbuf, 0xff, p->xbuf_bytes, st));
   PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
-  PAT_TRY_CUDA(persist2d_launch(p->R, adj, p->varc, a, p->ntiles, st));
+  if (p->sponge_w > 0)
+    PAT_TRY_CUDA(persist2d_launch_layer(p->R, adj, p->varc, a, p->ntiles, st));
+  else
+    PAT_TRY_CUDA(persist2d_launch(p->R, adj, p->varc, a, p->ntiles, st));
   return PAT_OK;
 }
 

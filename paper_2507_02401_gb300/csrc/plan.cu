@@ -569,13 +569,12 @@ pat_status pat_plan_set_path(pat_plan* plan, int path) {
     set_error("plan is NULL");
     return PAT_ERR_INVALID;
   }
-  const bool persist = plan->persist_ok && plan->sponge_w == 0;
+  const bool persist = plan->persist_ok;
   if (path == PAT_PATH_AUTO) {
     plan->path = persist ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
   } else if (path == PAT_PATH_PERSISTENT) {
     if (!persist) {
-      set_error("the persistent engine is not available for this plan (3D, too many tiles to co-reside, "
-                "or an absorbing layer)");
+      set_error("the persistent engine is not available for this plan (3D, or too many tiles to co-reside)");
       return PAT_ERR_INVALID;
     }
     plan->path = path;
@@ -632,9 +631,6 @@ pat_status pat_plan_set_sponge(pat_plan* plan, int width, double sigma_max, void
   if (width == 0) {
     plan->sponge_w = 0;
     plan->sponge_sigma_max = 0.0;
-    plan->path = plan->persist_ok ? PAT_PATH_PERSISTENT : PAT_PATH_STEP;
-    const char* env = getenv("PAT_WAVE_PATH");
-    if (env && strcmp(env, "step") == 0) plan->path = PAT_PATH_STEP;
     return PAT_OK;
   }
   // quadratic profile: within `width` cells of a face sigma = sigma_max ((width - d) / width)^2,
@@ -663,7 +659,6 @@ pat_status pat_plan_set_sponge(pat_plan* plan, int width, double sigma_max, void
   PAT_TRY_CUDA(cudaStreamSynchronize(st));
   plan->sponge_w = width;
   plan->sponge_sigma_max = smax;
-  plan->path = PAT_PATH_STEP;  // the persistent engine has no absorbing layer
   return PAT_OK;
 }
 

@@ -213,7 +213,11 @@ __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsign
   return false;
 }
 
-template <int R, bool ADJ, bool VARC>
+// SP: absorbing layer.  With per-cell factors a, b (1 outside the layer):
+//   forward  D' = a D + b inc (first step D' = (a-1) P + b inc), P' = P + D'
+//   adjoint  G' = G + inc, Q' = a Q + b G' (final x = ... + ((a-1)/b) Q); inside the layer the adjoint's
+//   compensation terms are carried approximately (the fields are being damped there).
+template <int R, bool ADJ, bool VARC, bool SP>
 __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persist2DArgs a) {
   using G = Geo<R, ADJ>;
   extern __shared__ float4 smem4[];
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   // forward: P, D ; adjoint: Q (in P), G (in D) and their compensation terms
   float P[2][4], D[2][4], K[2][4];
   float Pl[2][4], Dl[2][4], Kl[2][4];
+  float SA[2][4], SB[2][4];  // layer factors (SP only)
   bool valid[2][4];
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr)
@@ -258,6 +263,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       K[rr][j] = v ? (VARC ? a.kappa[gi] : a.kappa0) : 0.f;
       Kl[rr][j] = v ? (VARC ? a.kappa_lo[gi] : a.kappa0_lo) : 0.f;
       P[rr][j] = (!ADJ && v) ? a.in[gi] : 0.f;
+      SA[rr][j] = (SP && v) ? a.sp_a[gi] : 1.f;
+      SB[rr][j] = (SP && v) ? a.sp_b[gi] : 1.f;
       D[rr][j] = 0.f;
       Pl[rr][j] = 0.f;
       Dl[rr][j] = 0.f;
@@ -326,7 +333,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
           for (int j = 0; j < 4; ++j) {
             if (!valid[rr][j]) continue;
             const int lr = r0 + rr, lc = c0 + j;
-            const float xv = Jc[lr * TX + lc] + (D[rr][j] + Dl[rr][j]) + 0.5f * L[rr][j];
+            float xv = Jc[lr * TX + lc] + (D[rr][j] + Dl[rr][j]) + 0.5f * L[rr][j];
+            if (SP) xv = fmaf((SA[rr][j] - 1.f) / SB[rr][j], P[rr][j] + Pl[rr][j], xv);
             a.out[(long long)(gy0 + lr) * nx + gx0 + lc] = xv;
           }
       }
@@ -341,7 +349,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           // D += cf (kappa_hi + kappa_lo) L, the product rounded once before it meets D
-          D[rr][j] += fmaf(cf * K[rr][j], L[rr][j], (cf * Kl[rr][j]) * L[rr][j]);
+          const float inc = fmaf(cf * K[rr][j], L[rr][j], (cf * Kl[rr][j]) * L[rr][j]);
+          if (SP)
+            D[rr][j] = k == 0 ? fmaf(SA[rr][j] - 1.f, P[rr][j], SB[rr][j] * inc)
+                              : fmaf(SA[rr][j], D[rr][j], SB[rr][j] * inc);
+          else
+            D[rr][j] += inc;
           P[rr][j] += D[rr][j];
           V[rr][j] = P[rr][j];
           Vl[rr][j] = 0.f;
@@ -357,8 +370,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
           float e;
           float g = two_sum(D[rr][j], inc + Dl[rr][j], e);  // G += inc (compensated)
           float gl = e;
-          float q = two_sum(P[rr][j], g, e);  // Q += G (compensated)
-          float ql = Pl[rr][j] + e;
+          float q, ql;
+          if (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) {  // Q = a Q + b G inside the layer
+            q = fmaf(SA[rr][j], P[rr][j], SB[rr][j] * g);
+            ql = fmaf(SA[rr][j], Pl[rr][j], SB[rr][j] * gl);
+          } else {
+            q = two_sum(P[rr][j], g, e);  // Q += G (compensated)
+            ql = Pl[rr][j] + e;
+          }
           if (!valid[rr][j]) g = gl = q = ql = 0.f;
           D[rr][j] = g;
           Dl[rr][j] = gl;
@@ -390,16 +409,17 @@ __global__ void split_combine_kernel(const float* __restrict__ part, const int* 
   y[(long long)split_sensor[q] * nt + t] = ((p[0] + p[nt]) + p[2 * nt]) + p[3 * nt];
 }
 
-template <int R, bool ADJ, bool VARC>
+template <int R, bool ADJ, bool VARC, bool SP>
 void* kfn() {
-  return (void*)wave2d_persist_kernel<R, ADJ, VARC>;
+  return (void*)wave2d_persist_kernel<R, ADJ, VARC, SP>;
 }
 
-void* pick(int R, bool adj, bool varc) {
-#define PAT_P2D(RR)                                                       \
-  if (R == RR) {                                                          \
-    if (adj) return varc ? kfn<RR, true, true>() : kfn<RR, true, false>(); \
-    return varc ? kfn<RR, false, true>() : kfn<RR, false, false>();       \
+template <bool SP>
+void* pick_sp(int R, bool adj, bool varc) {
+#define PAT_P2D(RR)                                                               \
+  if (R == RR) {                                                                  \
+    if (adj) return varc ? kfn<RR, true, true, SP>() : kfn<RR, true, false, SP>(); \
+    return varc ? kfn<RR, false, true, SP>() : kfn<RR, false, false, SP>();       \
   }
   PAT_P2D(1)
   PAT_P2D(3)
@@ -408,6 +428,8 @@ void* pick(int R, bool adj, bool varc) {
 #undef PAT_P2D
   return nullptr;
 }
+
+void* pick(int R, bool adj, bool varc) { return pick_sp<false>(R, adj, varc); }
 
 size_t smem_bytes(int R, bool adj) {
   const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
@@ -446,6 +468,21 @@ int persist2d_max_ctas(int R, bool adj, bool varc) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj)) != cudaSuccess)
     return 0;
   return sms * per_sm;
+}
+
+cudaError_t persist2d_launch_layer(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {
+  void* f = pick_sp<true>(R, adj, varc);
+  if (!f) return cudaErrorInvalidValue;
+  int per_sm = 0, dev = 0, sms = 0;  // the layer variant must fit as many CTAs as the plan's tiles
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorUnknown;
+  cudaError_t e = prepare(f, R, adj);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj));
+  if (e != cudaSuccess) return e;
+  if (per_sm * sms < nctas) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj), st);
 }
 
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {

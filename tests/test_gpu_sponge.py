@@ -1,9 +1,10 @@
 """Absorbing layer on the GPU (pat_plan_set_sponge) against the FP64 oracle's
-damped program: K and K* (relative L2 <= 1e-5) through the TMA per-step
-kernel (orders 2 and 8, constant medium; order 4 varying medium, whose
-adjoint runs the compensated kernel) and the plain per-step kernel (nx not
-divisible by 4), short time axes, the default damping rate, a CG solve
-(<= 1e-4), the GPU dot-product identity, and the calls that refuse a layer."""
+damped program: K and K* (relative L2 <= 1e-5) through the persistent engine
+and the per-step engine (TMA kernel for orders 2 and 8 with a constant
+medium, order 4 varying medium whose adjoint runs the compensated kernel, the
+plain kernel for nx not divisible by 4), short time axes, the default
+damping rate, a CG solve (<= 1e-4), the GPU dot-product identity, and the
+calls that refuse a layer."""
 import numpy as np
 import pytest
 
@@ -32,13 +33,14 @@ def damped_pair(w, width, sigma_max):
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])) + f"-o{c[2]}" + ("v" if c[3] else ""))
-def test_sponge_forward_adjoint_parity(case):
+@pytest.mark.parametrize("path", [1, 2], ids=["persistent", "step"])
+def test_sponge_forward_adjoint_parity(case, path):
     need_gpu()
     shape, nt, order, varc, ns, width = case
     w = custom(shape, nt, order, varc, ns, seed=sum(shape) + order)
     smax = oracle.sponge_sigma_max(float(np.max(w.c_array())), width, w.h)
     plan, wave, _ = damped_pair(w, width, smax)
-    assert plan.path == 2
+    plan.path = path
     y = plan.forward(w.x_true).cpu().numpy()
     y_ref = wave.forward(w.x_true)
     assert rel(y, y_ref) <= TOL_OP
@@ -51,10 +53,12 @@ def test_sponge_forward_adjoint_parity(case):
 
 
 @pytest.mark.parametrize("nt", [1, 2, 3, 5])
-def test_sponge_short_time_axis(nt):
+@pytest.mark.parametrize("path", [1, 2], ids=["persistent", "step"])
+def test_sponge_short_time_axis(nt, path):
     need_gpu()
     w = custom((72, 136), nt, 8, False, 6, seed=nt)
     plan, wave, _ = damped_pair(w, 8, 0.4 / w.dt)
+    plan.path = path
     assert rel(plan.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= TOL_OP
     r = np.random.default_rng(nt).standard_normal((w.ns, nt))
     assert rel(plan.adjoint(r).cpu().numpy(), wave.adjoint(r)) <= TOL_OP
@@ -69,10 +73,11 @@ def test_sponge_default_rate_and_removal():
     b.set_sponge(10)  # default rate
     ya, yb = a.forward(w.x_true).cpu().numpy(), b.forward(w.x_true).cpu().numpy()
     assert rel(yb, ya) <= 1e-6
-    b.set_sponge(0)  # removed: the reflecting box again, default engine back
-    plain, wave, _ = make_pair(w)
-    assert b.path == plain.path
-    assert rel(b.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= TOL_OP
+    b.set_sponge(0)  # removed: the reflecting box again
+    _, wave, _ = make_pair(w)
+    for path in (1, 2):
+        b.path = path
+        assert rel(b.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= TOL_OP
 
 
 def test_sponge_dot_product_and_solve():
@@ -106,8 +111,6 @@ def test_sponge_refusals():
     with pytest.raises(_lib.PatError):
         p.set_sponge(-1)
     p.set_sponge(8)
-    with pytest.raises(_lib.PatError):
-        p.path = 1  # the persistent engine has no layer
     r = np.zeros((w.ns, w.nt))
     with pytest.raises(_lib.PatError):
         p.grad_kappa(w.x_true, r)
