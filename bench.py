@@ -79,7 +79,7 @@ WORKLOADS = {
                  "face, order-8 staggered FDTD, 2414 steps, data simulated on a 1024x1024 grid at half the time "
                  "step and sampled at every second step (no inverse crime), 2% noise, db4 5 levels, s = 1, "
                  "alpha = 1e-2 (relative), 15 GMRES iterations on the paper's image-space system"),
-        "kernel": "step2d_tma_kernel<R=7> with the absorbing layer",
+        "kernel": "wave2d_persist_kernel<R=7> with the absorbing layer",
         "profile": "step2d_tma_4096_o8.txt",
         "sources": ("wave2d_tma.cu", "stencil.cuh", "tma.cuh"),
         "oracle_nt": 40,
@@ -383,6 +383,7 @@ def run_ours(args):
     u = torch.empty(plan.N, device="cuda")
     x = torch.empty(w.shape, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    flush.zero_()  # first use outside the timed region (the first launch of a kernel loads its module)
 
     def solve(k, yy=y, xx=x, uu=u):
         s, alpha = combos[k % len(combos)]
@@ -573,13 +574,13 @@ def run_limited(args):
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
-    _lib.pat_plan_profile(plan.handle, 1)
     sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    flush.zero_()  # first use outside the timed region (the first launch of a kernel loads its module)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -590,8 +591,13 @@ def run_limited(args):
     barrier(world)
     clocks = sampler.stop() if sampler else None
     t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, True)
+    # wave-kernel durations and launch counts from one more solve with the library's measurement hooks
+    _lib.pat_plan_profile(plan.handle, 1)
+    solve()
+    torch.cuda.synchronize()
     kernels, wave_calls, wave_ms, points = _lib.pat_plan_profile_read(plan.handle)
     _lib.pat_plan_profile(plan.handle, 0)
+    kernels *= args.steps  # per timed solve, times the timed solves
     # end to end through the C ABI with host arrays
     x_host = np.zeros(w.shape, dtype=np.float32)
     torch.cuda.synchronize()
@@ -609,9 +615,10 @@ def run_limited(args):
         if s == s1:
             J_curve, res_curve = [float(v) for v in J], [float(v) for v in res]
     # algorithmic bytes of the step kernel per time step (12 B per point-update, constant medium)
-    launches = wave_calls * (w.nt - 1)
+    steps_per_launch = (w.nt - 1) if plan.path == 1 else 1
+    launches = wave_calls * (w.nt - 1) // steps_per_launch
     launch_ms = wave_ms / max(launches, 1)
-    achieved = 12.0 * w.N / (launch_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
+    achieved = 12.0 * w.N * steps_per_launch / (launch_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
     peak, peak_kind = peaks()
     # GMRES vector kernels besides the library's counted wave and wavelet kernels, per solve
     extra = 4 + sum(1 + 3 * (j + 1) + 3 for j in range(iters)) + 1 + iters
@@ -619,14 +626,16 @@ def run_limited(args):
         "metric": METRIC, "value": world * args.steps * iters / (t_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": spec["desc"], "engine": "step", "solver": "GMRES", "iters_per_step": iters,
+        "config": {"workload": spec["desc"], "engine": {1: "persistent", 2: "step"}.get(plan.path, "?"),
+                   "solver": "GMRES", "iters_per_step": iters,
                    "l2": "256 MiB buffer written before every step (inside the timed region)",
                    "parallelism": f"replicas x{world} (independent instances per rank)"},
         "rel_error_by_s": errs, "J_per_iterate_s1": J_curve, "residual_per_iterate_s1": res_curve,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "kernel": spec["kernel"],
                      "algorithmic_bytes_per_point_update": 12, "launch_ms": launch_ms, "launches_timed": launches,
-                     "launch": "one time step (averaged over whole K / K* applications, injection included)",
+                     "launch": "one K or K* application" if steps_per_launch > 1 else
+                               "one time step (averaged over whole K / K* applications, injection included)",
                      "note": "512^2 fields are L2-resident"},
         "e2e": {"value": world * args.steps * iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_np.nbytes),
                 "d2h_bytes_per_step": int(w.N * 4)},
@@ -679,6 +688,7 @@ def run_batch(args):
     alphas = [w.alpha[0] * lam for w, lam in zip(ws, lams)]
     xs = [torch.empty(w.shape, device="cuda") for w in ws]
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    flush.zero_()  # first use outside the timed region (the first launch of a kernel loads its module)
 
     def solve_batched():
         rc, per = _lib.pat_batch_solve(batch.handle, ys, alphas, ss, iters, xs, stream)

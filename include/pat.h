@@ -153,9 +153,9 @@ pat_status pat_solve(pat_plan* plan, const float* y, double alpha, double s, int
  * = 31 wave evaluations in its experiments) on the image-space system of
  * Eq. linear_minimization with the covariance Gamma = E_s E_s*:
  *   (Gamma K* K + alpha I) x = Gamma K* y,   x_0 = 0.
- * Arnoldi with modified Gram-Schmidt (FP32 basis vectors, FP64 inner
- * products reduced in a fixed order), Givens rotations and the Hessenberg
- * matrix on the host in FP64.  Converges to the same minimiser as pat_solve
+ * Arnoldi with classical Gram-Schmidt applied twice (FP32 basis vectors, FP64
+ * inner products reduced in a fixed order, all projections of a pass in one
+ * launch), Givens rotations and the Hessenberg matrix on the host in FP64.  Converges to the same minimiser as pat_solve
  * (x = E_s u).  Synchronous; allocates the (iters+1) x N basis per call.
  *   x    N floats (output; device or host).
  *   res  NULL or HOST array of iters+1 doubles: ||f - A x_k|| for k = 0..iters.

@@ -8,8 +8,10 @@
 // fixed order (per-block partial sums over a fixed grid, then one block sums
 // the partials in block order), so results are reproducible.  GMRES keeps its
 // (iters+1) x iters Hessenberg matrix and Givens rotations on the host in
-// FP64 (Arnoldi with modified Gram-Schmidt; the least-squares problem is
-// reduced by Givens rotations as the basis grows).
+// FP64 (Arnoldi with classical Gram-Schmidt applied twice, all projections of
+// a pass in one launch; the least-squares problem is reduced by Givens
+// rotations as the basis grows; one host synchronisation per iteration).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -74,6 +76,47 @@ __global__ void lw_update_kernel(float* __restrict__ u, const float* __restrict_
     const float ui = u[i];
     u[i] = fmaf(-omega, fmaf(alpha, ui, q[i]) - b[i], ui);
   }
+}
+
+// partial[i * KB + b] = block b's share of <V_i, w> for i = blockIdx.y (all basis vectors in one launch)
+__global__ void __launch_bounds__(KT) mdot_partial_kernel(const float* __restrict__ V, const float* __restrict__ w,
+                                                          long long n, double* __restrict__ partial) {
+  __shared__ double sh[KT / 32];
+  const float* v = V + (size_t)blockIdx.y * n;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT)
+    acc += (double)v[i] * (double)w[i];
+  const double s = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.y * KB + blockIdx.x] = s;
+}
+
+// h[i] (+)= sum of block partials of vector i (block i), in block order
+__global__ void __launch_bounds__(KT) mdot_final_kernel(const double* __restrict__ partial, double* __restrict__ h,
+                                                        int accumulate) {
+  __shared__ double sh[KT / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < KB; b += KT) v += partial[(size_t)blockIdx.x * KB + b];
+  const double s = block_reduce(v, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = accumulate ? h[blockIdx.x] + s : s;
+}
+
+// w -= sum_i c_i V_i with c the latest projection coefficients (device, FP64)
+__global__ void maxpy_kernel(float* __restrict__ w, const float* __restrict__ V, const double* __restrict__ c, int k,
+                             long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < k; ++i) acc -= c[i] * (double)V[(size_t)i * n + e];
+    w[e] = (float)acc;
+  }
+}
+
+// w /= sqrt(*nrm2) (left unchanged when the norm is zero)
+__global__ void normalize_kernel(float* __restrict__ w, const double* __restrict__ nrm2, long long n) {
+  const double s = *nrm2;
+  if (!(s > 0.0)) return;
+  const float inv = (float)(1.0 / sqrt(s));
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    w[e] *= inv;
 }
 
 int grid_of(long long n) {
@@ -161,9 +204,23 @@ pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int
     }
   }
   struct Free {
-    float* v;
+    void* v;
     ~Free() { cudaFree(v); }
   } guard{V};
+  // device scratch of the orthogonalisation: block partials of up to iters+1 inner products, the
+  // accumulated and per-pass coefficients and the norm
+  const int kk_max = iters + 1;
+  double* dP = nullptr;
+  {
+    const cudaError_t e = cudaMalloc(&dP, sizeof(double) * ((size_t)KB * kk_max + 2 * kk_max + 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("GMRES scratch: %s", cudaGetErrorString(e));
+      return PAT_ERR_OOM;
+    }
+  }
+  Free guard2{dP};
+  double* dH = dP + (size_t)KB * kk_max;
   auto Vj = [&](int j) { return V + (size_t)j * N; };
   // w = A v = E_s E_s* K* K v + alpha v
   auto apply_A = [&](const float* v, float* w) -> pat_status {
@@ -216,16 +273,29 @@ pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int
       continue;
     }
     PAT_TRY(apply_A(Vj(j), Vj(j + 1)));
-    for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
-      double hij = 0.0;
-      PAT_TRY(dot_host(p, Vj(i), Vj(j + 1), N, false, &hij, st));
-      h(i, j) = hij;
-      PAT_TRY_CUDA(axpy(Vj(j + 1), Vj(i), -hij, N, st));
+    // classical Gram-Schmidt applied twice (all projections of a pass in one launch, the second pass
+    // restores the orthogonality a single classical pass loses); column j of H and the new norm come
+    // back to the host in one copy
+    const int kk = j + 1;
+    double* hcol = dH;          // kk projection coefficients, accumulated over the two passes
+    double* c = dH + kk_max;    // this pass's coefficients
+    double* nrm = dH + 2 * kk_max;
+    for (int pass = 0; pass < 2; ++pass) {
+      mdot_partial_kernel<<<dim3(KB, kk), KT, 0, st>>>(V, Vj(j + 1), N, dP);
+      mdot_final_kernel<<<kk, KT, 0, st>>>(dP, c, 0);
+      maxpy_kernel<<<grid_of(N), 256, 0, st>>>(Vj(j + 1), V, c, kk, N);
+      mdot_final_kernel<<<kk, KT, 0, st>>>(dP, hcol, pass);  // hcol (+)= c
     }
-    double hn = 0.0;
-    PAT_TRY(dot_host(p, Vj(j + 1), Vj(j + 1), N, false, &hn, st));
-    hn = std::sqrt(hn);
-    if (hn > 0.0) PAT_TRY_CUDA(scal(Vj(j + 1), 1.0 / hn, N, st));
+    mdot_partial_kernel<<<dim3(KB, 1), KT, 0, st>>>(Vj(j + 1), Vj(j + 1), N, dP);
+    mdot_final_kernel<<<1, KT, 0, st>>>(dP, nrm, 0);
+    normalize_kernel<<<grid_of(N), 256, 0, st>>>(Vj(j + 1), nrm, N);
+    PAT_TRY_CUDA(cudaGetLastError());
+    std::vector<double> hv(kk + 1);
+    PAT_TRY_CUDA(cudaMemcpyAsync(hv.data(), hcol, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    PAT_TRY_CUDA(cudaMemcpyAsync(hv.data() + kk, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PAT_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < kk; ++i) h(i, j) = hv[i];
+    const double hn = std::sqrt(std::max(hv[kk], 0.0));
     // previous rotations on column j, then the one that zeroes h(j+1, j)
     for (int i = 0; i < j; ++i) {
       const double a = h(i, j), b = h(i + 1, j);
