@@ -138,6 +138,12 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
   } else if (p->tma3d && tma_ready(p, a)) {
     const long long nthr = tma3d_threads(p->n[0], p->n[1], p->n[2], p->tma3d_zchunk);
     if (y && a.ns > nthr) a.y = nullptr;
+    if (a.inj_r) {  // the adjoint's post-step injection, fused per CTA
+      a.inj_tile_ptr = p->d_tinj3_ptr;
+      a.inj_tile = p->d_tinj3;
+      a.ent_sensor = p->d_ent_sensor;
+      a.ent_w = p->d_ent_w;
+    }
     CUtensorMap mc, mp;
     const pat_plan::TmaDesc* dc = tma_desc(p, a.cur);
     if (!dc) return cudaErrorInvalidValue;
@@ -153,7 +159,12 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     const long long nthr =
         (long long)((p->n[0] + 31) / 32) * ((p->n[1] + 15) / 16) * ((p->n[2] + 31) / 32) * 128;
     if (y && a.ns > nthr) a.y = nullptr;
-    e = step3d_launch(p->R, adj, a, st);
+    StepArgs b = a;
+    b.inj_r = nullptr;
+    e = step3d_launch(p->R, adj, b, st);
+    if (e == cudaSuccess && a.inj_r)  // the adjoint's injection after the step
+      e = inject_launch(a.next, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, a.inj_r, p->nt,
+                        a.inj_t, 1.f, st);
   }
   if (e == cudaSuccess && y && !a.y)
     e = sample_launch(a.cur, p->ns, p->nt, a.t_sample, p->d_sens_cell, p->d_sens_w, p->corners, y, st);
@@ -264,6 +275,7 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
   auto Qbuf = [&](int m) { return p->d_wv[(nt - 1 - m) % 3]; };
   PAT_TRY_CUDA(fill_launch(Qbuf(nt - 1), p->N, 0.f, st));
   PAT_TRY_CUDA(inject(Qbuf(nt - 1), nt - 1));
+  a.inj_r = y;  // S^T r_m added to Q^m by (or just after) the step that makes it
   for (int m = nt - 2; m >= 1; --m) {
     a.cur = Qbuf(m + 1);
     a.prev = (m + 2 <= nt - 1) ? Qbuf(m + 2) : nullptr;
@@ -271,8 +283,8 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
     a.c_cur = 2.f;
     a.c_prev = 1.f;
     a.c_lap = 1.f;
+    a.inj_t = m;
     PAT_TRY_CUDA(step_launch(p, true, a, st));
-    PAT_TRY_CUDA(inject(Qbuf(m), m));
   }
   a.cur = Qbuf(1);
   a.prev = (nt >= 3) ? Qbuf(2) : nullptr;
@@ -280,8 +292,8 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
   a.c_cur = 1.f;
   a.c_prev = 1.f;
   a.c_lap = 0.5f;
+  a.inj_t = 0;
   PAT_TRY_CUDA(step_launch(p, true, a, st));
-  PAT_TRY_CUDA(inject(x, 0));
   return PAT_OK;
 }
 
@@ -304,6 +316,7 @@ static long long wave_kernels(const pat_plan* p, bool adj) {
   const long long inj = p->n_inj > 0 ? 1 : 0;
   if (p->dim == 2 && p->tma2d && !p->varc && p->R <= 3) return 4 + (nt - 1) + 1;  // 4 fills, fused injection
   if (p->dim == 2) return 4 + (nt - 1) * (1 + inj) + (1 + inj);  // 4 fills, (inject+step) x (nt-1), final
+  if (p->tma3d) return (1 + inj) + (nt - 2) + 1;                   // fill+inject, steps with fused injection
   return (1 + inj) + (nt - 2) * (1 + inj) + (1 + inj);             // fill+inject, (step+inject), final
 }
 

@@ -506,6 +506,28 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
       p->tma3d_zchunk = tma3d_zchunk(p->n[0], p->n[1], p->n[2]);
     }
   }
+  if (p->tma3d) {  // injection lists per CTA of the 3D TMA grid (the adjoint injects after each step)
+    const int nx = p->n[0], ny = p->n[1], zc = p->tma3d_zchunk;
+    const int bx = (nx + 63) / 64, by = (ny + 15) / 16, bz = (p->n[2] + zc - 1) / zc;
+    std::vector<std::vector<InjCell>> bins((size_t)bx * by * bz);
+    for (int i = 0; i < p->n_inj; ++i) {
+      const long long c = p->h_inj_cell[i];
+      const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+      bins[((size_t)(z / zc) * by + y / 16) * bx + x / 64].push_back(InjCell{(int)c, p->h_inj_ptr[i], p->h_inj_ptr[i + 1]});
+    }
+    std::vector<int> ptr(1, 0);
+    std::vector<InjCell> cells;
+    for (auto& b : bins) {
+      cells.insert(cells.end(), b.begin(), b.end());
+      ptr.push_back((int)cells.size());
+    }
+    PAT_TRY(alloc_n(p, &p->d_tinj3_ptr, ptr.size(), "CTA injection lists"));
+    PAT_TRY(alloc_n(p, &p->d_tinj3, std::max<size_t>(cells.size(), 1), "CTA injection lists"));
+    PAT_TRY_CUDA(cudaMemcpyAsync(p->d_tinj3_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st));
+    if (!cells.empty())
+      PAT_TRY_CUDA(cudaMemcpyAsync(p->d_tinj3, cells.data(), sizeof(InjCell) * cells.size(), cudaMemcpyHostToDevice,
+                                   st));
+  }
   PAT_TRY_CUDA(cudaStreamSynchronize(st));
   return PAT_OK;
 }

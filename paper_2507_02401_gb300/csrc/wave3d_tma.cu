@@ -50,7 +50,8 @@ __device__ __forceinline__ void fused_sample3(const StepArgs& a, long long gtid)
   a.y[(long long)s * a.nt + a.t_sample] = v;
 }
 
-template <int R>
+// INJ: the adjoint's injection S^T r_m into the CTA's own cells of `next` after the step (per-CTA lists)
+template <int R, bool INJ>
 __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mcur,
                                                              const __grid_constant__ CUtensorMap mprev, int zchunk,
                                                              int* status, long long timeout_ns) {
@@ -173,6 +174,16 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
     }
     __syncthreads();  // the centre slot is refilled by the next iteration's TMA
   }
+  if (INJ && ok_all) {  // every thread's stores to `next` precede the injection (same CTA)
+    __syncthreads();
+    for (int e = a.inj_tile_ptr[bid] + t; e < a.inj_tile_ptr[bid + 1]; e += THREADS) {
+      const InjCell c = a.inj_tile[e];
+      float v = 0.f;
+      for (int q = c.beg; q < c.end; ++q)
+        v = fmaf(a.ent_w[q], a.inj_r[(long long)a.ent_sensor[q] * a.nt + a.inj_t], v);
+      a.next[c.local] += v;
+    }
+  }
   // after a timed-out wait: give the copies still in flight (the last one of
   // each slot) a bounded chance to land before the CTA's shared memory goes away
   if (t == 0 && !ok_all) {
@@ -182,19 +193,31 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
   }
 }
 
-template <int R>
+template <int R, bool INJ>
 cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int zchunk, int* status,
                      long long timeout_ns, cudaStream_t st) {
   const size_t smem = G3<R>::SMEM;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
-  step3d_tma_kernel<R><<<grid, THREADS, smem, st>>>(a, mc, mp, zchunk, status, timeout_ns);
+  step3d_tma_kernel<R, INJ><<<grid, THREADS, smem, st>>>(a, mc, mp, zchunk, status, timeout_ns);
   return cudaGetLastError();
+}
+
+template <bool INJ>
+cudaError_t launch_i(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+                     int* status, long long timeout_ns, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_r<1, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 3: return launch_r<3, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 5: return launch_r<5, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 7: return launch_r<7, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -252,13 +275,8 @@ long long tma3d_threads(int nx, int ny, int nz, int zchunk) {
 
 cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
                               int* status, long long timeout_ns, cudaStream_t st) {
-  switch (R) {
-    case 1: return launch_r<1>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 3: return launch_r<3>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 5: return launch_r<5>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 7: return launch_r<7>(a, cur, prev, zchunk, status, timeout_ns, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return a.inj_r ? launch_i<true>(R, a, cur, prev, zchunk, status, timeout_ns, st)
+                 : launch_i<false>(R, a, cur, prev, zchunk, status, timeout_ns, st);
 }
 
 }  // namespace pat
