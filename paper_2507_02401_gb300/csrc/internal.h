@@ -158,11 +158,12 @@ cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, 
 bool tma2d_supported(int nx, int R);
 // P boxes (80 x (64+2R)) and own-tile boxes (64 x 64) of an nx x ny float field
 cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* halo, CUtensorMap* own);
-// mode 0: constant medium, 1: varying medium (forward), 2: constant medium with fused injection (adjoint);
+// mode 0: constant medium, 1: varying medium (forward), 2: constant medium with fused injection (adjoint),
+// 3: varying-medium adjoint (k: kappa's halo-box descriptor, unused by the other modes);
 // sp 0: no absorbing layer, 1: layer with the forward update, 2: layer with the adjoint update
 long long tma2d_threads(int nx, int ny, int R, int mode, int sp);  // threads of one launch (fused sampling)
-cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, int* status,
-                              long long timeout_ns, cudaStream_t st);
+cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& k,
+                              int* status, long long timeout_ns, cudaStream_t st);
 
 // wave_step.cu
 cudaError_t step2d_launch(int R, bool adj, const StepArgs& a, cudaStream_t st);

@@ -98,13 +98,14 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
   // sample separately when the step grid has fewer threads than sensors
   float* y = a.y;
   cudaError_t e;
-  if (p->dim == 2 && p->tma2d && !(adj && p->varc) && tma_ready(p, a)) {
-    // forward, and the constant-medium adjoint (same recurrence): TMA tile pipelines
+  if (p->dim == 2 && p->tma2d && tma_ready(p, a)) {
+    // TMA tile pipelines: forward; constant-medium adjoint (same recurrence); varying-medium adjoint
+    // with kappa Q formed in shared memory
     const bool varc = p->varc && !adj;
     // injection fused for radius <= 3; at radius 5-7 the fused variant's code generation is slower than
     // mode 0 plus a separate injection launch on every grid measured (2048^2 .. 16384^2)
-    const bool fuse = a.inj_r && p->R <= 3;
-    const int mode = varc ? 1 : (fuse ? 2 : 0);
+    const bool fuse = a.inj_r && p->R <= 3 && !p->varc;
+    const int mode = varc ? 1 : (adj && p->varc ? 3 : (fuse ? 2 : 0));
     const int sp = p->sponge_w > 0 ? (adj ? 2 : 1) : 0;
     const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, mode, sp);
     if (y && a.ns > nthr) a.y = nullptr;
@@ -123,7 +124,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
       if (e != cudaSuccess) return e;
       b.inj_r = nullptr;
     }
-    e = step2d_tma_launch(p->R, mode, sp, b, dp->halo, p->d_status, p->timeout_ns, st);
+    e = step2d_tma_launch(p->R, mode, sp, b, dp->halo, p->tma_kappa, p->d_status, p->timeout_ns, st);
   } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;

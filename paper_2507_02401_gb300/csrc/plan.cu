@@ -473,6 +473,8 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   if (p->dim == 2 && tma2d_supported(p->n[0], p->R) && !(env2 && strcmp(env2, "plain") == 0)) {
     CUtensorMap mh, mo;
     if (tma2d_encode(p->d_wv[0], p->n[0], p->n[1], p->R, &mh, &mo) == cudaSuccess) p->tma2d = true;
+    if (p->tma2d && p->varc && tma2d_encode(p->d_kappa, p->n[0], p->n[1], p->R, &p->tma_kappa, &mo) != cudaSuccess)
+      p->tma2d = false;
   }
   if (p->tma2d) {  // injection lists per 64 x 64 tile for the fused adjoint injection (tile-local cells)
     const int tx = (p->n[0] + 63) / 64, ntl = tx * ((p->n[1] + 63) / 64);

@@ -34,11 +34,11 @@ constexpr int TCOLS = TX / 4, TROWS = TY / RUN, THREADS = TCOLS * TROWS;  // 16 
 constexpr int XH = 8;            // box columns left of the tile (>= R, 16-byte aligned)
 constexpr int BW = TX + 2 * XH;  // P box width, 80 floats
 
-template <int R>
+template <int R, int NBOX = 1>
 struct G2 {
   static constexpr int BH = TY + 2 * R;
   static constexpr int PBOX = BW * BH;  // floats (multiple of 32: 128-byte aligned)
-  static constexpr int STAGE = PBOX;
+  static constexpr int STAGE = NBOX * PBOX;  // mode 3 stages the field and kappa
   static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
 };
 
@@ -51,7 +51,10 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
 }
 
 // MODE 0: constant medium; 1: varying medium (forward); 2: constant medium with the adjoint's
-// injection S^T r_m fused (a separate instance, so the other modes keep their code generation).
+// injection S^T r_m fused (a separate instance, so the other modes keep their code generation);
+// 3: varying-medium adjoint, G' = G + c_lap L(kappa Q), Q' = Q + G': the stage holds boxes of Q and
+// kappa, turned into W = kappa Q in shared memory before the stencil (uncompensated: FP32 emulation
+// of the 512^2 / 1500-step order-8 workload gives 2.4e-6 against 1.5e-6 with TwoSum compensation).
 // SP 0: no absorbing layer; 1: layer, forward update; 2: layer, adjoint update.  With the layer's
 // per-cell factors a = (1-q)/(1+q), b = 1/(1+q), q = sigma dt/2:
 //   forward  D' = a D + b inc (first step: D' = (a-1) P + b inc),  P' = P + D'
@@ -59,9 +62,10 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
 // Tiles that do not reach the layer use a = b = 1 without loading the factors.
 template <int R, int MODE, int SP>
 __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
-                                                             int* status, long long timeout_ns) {
-  using G = G2<R>;
-  constexpr bool VARC = MODE == 1, INJ = MODE == 2;
+                                                             const __grid_constant__ CUtensorMap mk, int* status,
+                                                             long long timeout_ns) {
+  constexpr bool VARC = MODE == 1, INJ = MODE == 2, WK = MODE == 3;
+  using G = G2<R, WK ? 2 : 1>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
   const int ntiles = tiles_x * ((ny + TY - 1) / TY);
   const int c0 = (t % TCOLS) * 4, r0 = (t / TCOLS) * RUN;
   const bool load_d = !a.d_zero;
-  const unsigned stage_bytes = (unsigned)G::PBOX * 4u;
+  const unsigned stage_bytes = (unsigned)G::STAGE * 4u;
 
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -91,6 +95,7 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
     const int gx0 = (tile % tiles_x) * TX, gy0 = (tile / tiles_x) * TY;
     mbar_expect_tx(&bars[s], stage_bytes);
     tma_load_2d(st, &mp, gx0 - XH, gy0 - R, &bars[s]);
+    if (WK) tma_load_2d(st + G::PBOX, &mk, gx0 - XH, gy0 - R, &bars[s]);
   };
   int first = blockIdx.x;
   if (t == 0 && first < ntiles) issue(first, 0);
@@ -145,7 +150,21 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
       ok = false;
       break;
     }
-    const float* P = stage0 + s * G::STAGE;
+    float* Pw = stage0 + s * G::STAGE;
+    const float* P = Pw;
+    float4 qown[RUN];  // mode 3: this thread's own Q cells (the box becomes W = kappa Q)
+    if (WK) {
+#pragma unroll
+      for (int rr = 0; rr < RUN; ++rr) qown[rr] = *reinterpret_cast<const float4*>(P + (r0 + rr + R) * BW + XH + c0);
+      __syncthreads();
+      float4* W4 = reinterpret_cast<float4*>(Pw);
+      const float4* K4 = reinterpret_cast<const float4*>(Pw + G::PBOX);
+      for (int i = t; i < G::PBOX / 4; i += THREADS) {
+        const float4 q = W4[i], kk = K4[i];
+        W4[i] = make_float4(kk.x * q.x, kk.y * q.y, kk.z * q.z, kk.w * q.w);
+      }
+      __syncthreads();
+    }
     // absorbing layer: does the tile reach it (its factors are then loaded row by row)
     const bool layer = SP != 0 && (gx0 < a.sp_w || gx0 + TX > nx - a.sp_w || gy0 < a.sp_w || gy0 + TY > ny - a.sp_w);
     if (INJ && inj_e > inj_b) {  // G += S^T r_m in the owners' registers; the shared tile is cleared again
@@ -202,13 +221,16 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
   #pragma unroll
           for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<false>(f[8 + j + m], f[8 + j - m], c, c2), acc);
           float inc;
-          if (VARC)
+          if (WK)
+            inc = a.c_lap * acc;  // kappa is inside the stencil field
+          else if (VARC)
             inc = fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc);
           else
             inc = fmaf(ckh, acc, ckl * acc);
+          const float qv = WK ? f4get(qown[rr], j) : c;  // the stepped field at this cell
           if (!LAYER) {
             dn[j] = f4get(d4[rr], j) + inc;
-            pn[j] = a.final_step ? dn[j] : c + dn[j];
+            pn[j] = a.final_step ? dn[j] : qv + dn[j];
           } else if (SP == 1) {  // forward in the layer
             const float fa = f4get(sa4, j), fb = f4get(sb4, j);
             dn[j] = load_d ? fmaf(fa, f4get(d4[rr], j), fb * inc) : fmaf(fa - 1.f, c, fb * inc);
@@ -216,7 +238,7 @@ __global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, c
           } else {  // adjoint in the layer
             const float fa = f4get(sa4, j), fb = f4get(sb4, j);
             dn[j] = f4get(d4[rr], j) + inc;
-            pn[j] = a.final_step ? fmaf((fa - 1.f) / fb, c, dn[j]) : fmaf(fa, c, fb * dn[j]);
+            pn[j] = a.final_step ? fmaf((fa - 1.f) / fb, qv, dn[j]) : fmaf(fa, qv, fb * dn[j]);
           }
         }
         if (in) {
@@ -253,7 +275,9 @@ const void* kernel_r(int mode, int sp) {
     case 4: return kfn<R, 1, 1>();
     case 6: return kfn<R, 2, 0>();
     case 8: return kfn<R, 2, 2>();
-    default: return nullptr;  // varying-medium adjoint and mismatched layer modes are not instantiated
+    case 9: return kfn<R, 3, 0>();
+    case 11: return kfn<R, 3, 2>();
+    default: return nullptr;  // mismatched layer modes are not instantiated
   }
 }
 
@@ -268,7 +292,9 @@ const void* kernel_for(int R, int mode, int sp) {
 }
 
 size_t smem_for(int R, int mode) {
-  const size_t base = R == 1 ? G2<1>::SMEM : R == 3 ? G2<3>::SMEM : R == 5 ? G2<5>::SMEM : G2<7>::SMEM;
+  const size_t base = mode == 3 ? (R == 1 ? G2<1, 2>::SMEM : R == 3 ? G2<3, 2>::SMEM : R == 5 ? G2<5, 2>::SMEM
+                                                                                       : G2<7, 2>::SMEM)
+                                : (R == 1 ? G2<1>::SMEM : R == 3 ? G2<3>::SMEM : R == 5 ? G2<5>::SMEM : G2<7>::SMEM);
   return base + (mode == 2 ? sizeof(float) * TX * TY : 0);
 }
 
@@ -297,7 +323,7 @@ cudaError_t tma2d_encode(const float* base, int nx, int ny, int R, CUtensorMap* 
 
 // Persistent grid: as many CTAs as fit on the device, at most one per tile.
 int tma2d_ctas(int nx, int ny, int R, int mode, int sp) {
-  static int cached[3][3][8] = {{{0}}};
+  static int cached[4][3][8] = {{{0}}};
   int& c = cached[mode][sp][R];
   if (!c) {
     int dev = 0, sms = 148, per = 1;
@@ -322,14 +348,14 @@ long long tma2d_threads(int nx, int ny, int R, int mode, int sp) {
   return (long long)tma2d_ctas(nx, ny, R, mode, sp) * THREADS;
 }
 
-cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, int* status,
-                              long long timeout_ns, cudaStream_t st) {
+cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& k,
+                              int* status, long long timeout_ns, cudaStream_t st) {
   const void* fn = kernel_for(R, mode, sp);
   if (!fn) return cudaErrorInvalidValue;
   const int nctas = tma2d_ctas(a.nx, a.ny, R, mode, sp);  // sets the kernel's attributes once
-  CUtensorMap map = p;
+  CUtensorMap map = p, mapk = k;
   StepArgs args = a;
-  void* params[] = {&args, &map, &status, &timeout_ns};
+  void* params[] = {&args, &map, &mapk, &status, &timeout_ns};
   return cudaLaunchKernel(fn, dim3(nctas), dim3(THREADS), params, smem_for(R, mode), st);
 }
 

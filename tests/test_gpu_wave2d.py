@@ -5,7 +5,7 @@ span several 64 x 64 tiles with ragged edges, every stencil order, constant
 and varying media (the varying-medium adjoint keeps the compensated kernel),
 short time axes, a field address the kernel cannot take (it falls back per
 step), agreement with the plain per-step kernel, the medium gradient, and
-the full-size 512 x 512 order-8 varying-medium forward map."""
+the full-size 512 x 512 order-8 varying-medium forward map and adjoint."""
 import numpy as np
 import pytest
 
@@ -59,7 +59,9 @@ def test_tma2d_matches_plain_kernel(monkeypatch, varc):
     monkeypatch.delenv("PAT_STEP2D")
     assert rel(a.forward(w.x_true).cpu().numpy(), b.forward(w.x_true).cpu().numpy()) <= 2e-6
     r = np.random.default_rng(1).standard_normal((w.ns, w.nt))
-    assert rel(a.adjoint(r).cpu().numpy(), b.adjoint(r).cpu().numpy()) <= 2e-6
+    # the varying-medium adjoint of the TMA kernel is uncompensated, the plain kernel's compensated:
+    # both are held to the operator bound against the oracle, so compare them at that bound
+    assert rel(a.adjoint(r).cpu().numpy(), b.adjoint(r).cpu().numpy()) <= (1e-5 if varc else 2e-6)
 
 
 def test_tma2d_unaligned_field_falls_back():
@@ -93,3 +95,14 @@ def test_tma2d_vessels_512_forward_full_size():
     w = synth.workload("vessels")
     plan, wave, _ = make_pair(w, path=2)
     assert rel(plan.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= TOL_OP
+
+
+def test_tma2d_vessels_512_adjoint_full_size():
+    """The varying-medium adjoint through the TMA kernel (kappa Q formed in shared memory,
+    uncompensated) at the full 512 x 512, order 8, 1500-step workload with random data."""
+    need_gpu()
+    w = synth.workload("vessels")
+    plan, wave, _ = make_pair(w, path=2)
+    r = np.random.default_rng(2).standard_normal((w.ns, w.nt))
+    assert rel(plan.adjoint(r).cpu().numpy(), wave.adjoint(r)) <= TOL_OP
+
