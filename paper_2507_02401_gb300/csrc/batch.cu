@@ -30,7 +30,7 @@ void bfree_all(pat_batch* b) {
   for (void* p : b->allocations) cudaFree(p);
   b->allocations.clear();
   b->d_inst = nullptr;
-  b->d_tile_inst = nullptr;
+  b->d_tiles = nullptr;
   b->d_maps = nullptr;
   b->d_status = nullptr;
 }
@@ -62,8 +62,8 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
   const int TX = 64, TY = batch_tile_y(variant);
   const int B = b->B;
   std::vector<BInst> inst(B);
-  std::vector<int> tile_inst;
-  std::vector<std::vector<int>> samp_ptr(B), samp(B), inj_ptr(B);
+  std::vector<BTile> tiles;
+  std::vector<std::vector<int>> samp(B);
   std::vector<std::vector<InjCell>> inj(B);
   for (int k = 0; k < B; ++k) {
     const pat_plan* p = b->plans[b->order[k]];
@@ -75,7 +75,7 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     I.ny = ny;
     I.nt = p->nt;
     I.tiles_x = tx;
-    I.tile0 = (int)tile_inst.size();
+    I.tile0 = (int)tiles.size();
     I.ns = p->ns;
     I.corners = p->corners;
     I.kappa0 = p->kappa0;
@@ -89,23 +89,28 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     I.sens_w = p->d_sens_w;
     I.ent_sensor = p->d_ent_sensor;
     I.ent_w = p->d_ent_w;
-    tile_inst.insert(tile_inst.end(), nt_tiles, k);
     auto tile_of = [&](int cell) { return ((cell / nx) / TY) * tx + (cell % nx) / TX; };
     std::vector<std::vector<int>> sb(nt_tiles);
     for (int s = 0; s < p->ns; ++s) sb[tile_of(p->h_sens_cell[(size_t)s * p->corners])].push_back(s);
     std::vector<std::vector<InjCell>> ib(nt_tiles);
     for (int i = 0; i < p->n_inj; ++i)
       ib[tile_of(p->h_inj_cell[i])].push_back(InjCell{p->h_inj_cell[i], p->h_inj_ptr[i], p->h_inj_ptr[i + 1]});
-    samp_ptr[k].push_back(0);
-    inj_ptr[k].push_back(0);
     for (int tl = 0; tl < nt_tiles; ++tl) {
+      BTile d{};
+      d.inst = k;
+      d.gx0 = (tl % tx) * TX;
+      d.gy0 = (tl / tx) * TY;
+      d.lt = tl;
+      d.s0 = (int)samp[k].size();
       samp[k].insert(samp[k].end(), sb[tl].begin(), sb[tl].end());
-      samp_ptr[k].push_back((int)samp[k].size());
+      d.s1 = (int)samp[k].size();
+      d.j0 = (int)inj[k].size();
       inj[k].insert(inj[k].end(), ib[tl].begin(), ib[tl].end());
-      inj_ptr[k].push_back((int)inj[k].size());
+      d.j1 = (int)inj[k].size();
+      tiles.push_back(d);
     }
   }
-  b->ntiles = (int)tile_inst.size();
+  b->ntiles = (int)tiles.size();
   // tiles running at global step t: instances with nt > t (a prefix, longest first)
   b->active.assign(b->max_nt, 0);
   for (int k = 0; k < B; ++k) {
@@ -114,21 +119,15 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
   }
   // per-instance lists in device memory
   for (int k = 0; k < B; ++k) {
-    int *dsp, *ds, *dip;
+    int* ds;
     InjCell* di;
-    PAT_TRY(balloc(b, &dsp, samp_ptr[k].size(), "batch sampling lists"));
     PAT_TRY(balloc(b, &ds, samp[k].size(), "batch sampling lists"));
-    PAT_TRY(balloc(b, &dip, inj_ptr[k].size(), "batch injection lists"));
     PAT_TRY(balloc(b, &di, inj[k].size(), "batch injection lists"));
-    PAT_TRY_CUDA(cudaMemcpyAsync(dsp, samp_ptr[k].data(), sizeof(int) * samp_ptr[k].size(), cudaMemcpyHostToDevice, st));
     if (!samp[k].empty())
       PAT_TRY_CUDA(cudaMemcpyAsync(ds, samp[k].data(), sizeof(int) * samp[k].size(), cudaMemcpyHostToDevice, st));
-    PAT_TRY_CUDA(cudaMemcpyAsync(dip, inj_ptr[k].data(), sizeof(int) * inj_ptr[k].size(), cudaMemcpyHostToDevice, st));
     if (!inj[k].empty())
       PAT_TRY_CUDA(cudaMemcpyAsync(di, inj[k].data(), sizeof(InjCell) * inj[k].size(), cudaMemcpyHostToDevice, st));
-    inst[k].samp_ptr = dsp;
     inst[k].samp = ds;
-    inst[k].inj_ptr = dip;
     inst[k].inj = di;
   }
   std::vector<CUtensorMap> maps(3 * (size_t)B);
@@ -139,13 +138,12 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     PAT_TRY_CUDA(batch_encode(I.img, I.nx, I.ny, b->R, variant, &maps[3 * k + 2]));
   }
   PAT_TRY(balloc(b, &b->d_inst, (size_t)B, "batch instances"));
-  PAT_TRY(balloc(b, &b->d_tile_inst, tile_inst.size(), "batch tile table"));
+  PAT_TRY(balloc(b, &b->d_tiles, tiles.size(), "batch tile table"));  // cudaMalloc: 16-byte aligned entries
   PAT_TRY(balloc(b, &b->d_maps, maps.size(), "batch tensor maps"));  // cudaMalloc: 256-byte aligned
   PAT_TRY(balloc(b, &b->d_status, 1, "batch status"));
   PAT_TRY_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_inst, inst.data(), sizeof(BInst) * B, cudaMemcpyHostToDevice, st));
-  PAT_TRY_CUDA(cudaMemcpyAsync(b->d_tile_inst, tile_inst.data(), sizeof(int) * tile_inst.size(),
-                               cudaMemcpyHostToDevice, st));
+  PAT_TRY_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BTile) * tiles.size(), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
   b->nctas = batch_max_ctas(b->R, variant);
@@ -159,7 +157,7 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
 BatchStepArgs step_args(const pat_batch* b, int t, bool adjoint) {
   BatchStepArgs a{};
   a.inst = b->d_inst;
-  a.tile_inst = b->d_tile_inst;
+  a.tiles = b->d_tiles;
   a.maps = b->d_maps;
   a.t = t;
   a.adjoint = adjoint ? 1 : 0;

@@ -20,17 +20,24 @@ struct BInst {
   float* y;          // sensor data: forward output, adjoint input (ns x nt)
   const int* sens_cell;
   const float* sens_w;
-  const int* samp_ptr;  // per local tile: range into samp (sensors whose base cell is in the tile)
-  const int* samp;
-  const int* inj_ptr;   // per local tile: range into inj (injected cells of the tile)
-  const InjCell* inj;   // .local holds the cell's linear index
+  const int* samp;       // sensors grouped by the tile holding their base cell
+  const InjCell* inj;    // injected cells grouped by tile; .local holds the cell's linear index
   const int* ent_sensor;
   const float* ent_w;
 };
 
+// One entry of the tile table (32 bytes, read as two 16-byte words).
+struct alignas(16) BTile {
+  int inst;        // instance slot
+  int gx0, gy0;    // tile origin in the instance's grid
+  int lt;          // tile index within the instance
+  int s0, s1;      // range into the instance's samp list (forward sampling)
+  int j0, j1;      // range into the instance's inj list (adjoint injection)
+};
+
 struct BatchStepArgs {
   const BInst* inst;
-  const int* tile_inst;       // tile -> instance
+  const BTile* tiles;         // tile table
   const CUtensorMap* maps;    // 3 per instance: P[0], P[1], img (halo boxes)
   int t;                      // global step: forward n = t, adjoint m = nt - 1 - t
   int adjoint;
@@ -58,7 +65,7 @@ struct pat_batch {
   int B = 0, R = 1, variant = 0, nctas = 0, max_nt = 0, ntiles = 0;
   std::vector<int> active;       // active[t]: tiles still running at global step t
   pat::BInst* d_inst = nullptr;
-  int* d_tile_inst = nullptr;
+  pat::BTile* d_tiles = nullptr;
   CUtensorMap* d_maps = nullptr;
   int* d_status = nullptr;       // timeout of a bounded wait in the batched kernel
   long long timeout_ns = 2000000000LL;

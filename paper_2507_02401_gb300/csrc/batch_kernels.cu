@@ -14,7 +14,10 @@
 // kernel: TMA halo boxes of P in two shared-memory stages, D in registers, a
 // sliding y window per thread.  Sampling and injection are fused per tile
 // (each tile samples the sensors whose base cell it holds and injects into
-// its own cells).
+// its own cells).  Each tile's descriptor (instance, origin, list ranges) is
+// read two tiles ahead of its use, so the only loads left between the end of
+// one tile and the stencil of the next are the tile's own D cells and the
+// TMA box issued one tile ahead.
 #include <mutex>
 
 #include "batch.h"
@@ -53,35 +56,45 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
   }
   __syncthreads();
 
-  // halo box of the field the tile's stencil reads at this step
-  auto issue = [&](int tile, int s) {
-    const int ii = a.tile_inst[tile];
-    const BInst& I = a.inst[ii];
-    const int lt = tile - I.tile0;
-    const int gx0 = (lt % I.tiles_x) * TX, gy0 = (lt / I.tiles_x) * TY;
-    const CUtensorMap* map = a.maps + 3 * ii + ((!adj && step == 0) ? 2 : (step & 1));
-    mbar_expect_tx(&bars[s], (unsigned)G::PBOX * 4u);
-    tma_load_2d(stage0 + s * G::PBOX, map, gx0 - XH, gy0 - R, &bars[s]);
+  // tile descriptor in registers: instance, origin and the list range of this direction
+  // (an empty descriptor past the active prefix)
+  struct Desc {
+    int inst, gx0, gy0, e0, e1;
   };
-  if (t == 0 && (int)blockIdx.x < a.active) issue(blockIdx.x, 0);
+  auto desc = [&](int tile) {
+    Desc d{0, 0, 0, 0, 0};
+    if (tile < a.active) {
+      const int4* p = reinterpret_cast<const int4*>(a.tiles + tile);
+      const int4 u = __ldg(p), v = __ldg(p + 1);
+      d = Desc{u.x, u.y, u.z, adj ? v.z : v.x, adj ? v.w : v.y};
+    }
+    return d;
+  };
+  // halo box of the field the tile's stencil reads at this step
+  auto issue = [&](const Desc& d, int s) {
+    const CUtensorMap* map = a.maps + 3 * d.inst + ((!adj && step == 0) ? 2 : (step & 1));
+    mbar_expect_tx(&bars[s], (unsigned)G::PBOX * 4u);
+    tma_load_2d(stage0 + s * G::PBOX, map, d.gx0 - XH, d.gy0 - R, &bars[s]);
+  };
+  Desc dc = desc(blockIdx.x), dn = desc(blockIdx.x + gridDim.x);
+  if (t == 0 && (int)blockIdx.x < a.active) issue(dc, 0);
 
   int k = 0, issued = ((int)blockIdx.x < a.active) ? 1 : 0;
   bool ok = true;
   for (int tile = blockIdx.x; tile < a.active; tile += gridDim.x, ++k) {
     const int s = k & 1;
+    const int nxt = tile + gridDim.x;
+    const Desc dnn = desc(nxt + gridDim.x);  // consumed two tiles from now
     if (t == 0) {
       fence_proxy_async_shared();  // the other stage was last read through the generic proxy
-      const int nxt = tile + gridDim.x;
       if (nxt < a.active) {
-        issue(nxt, s ^ 1);
+        issue(dn, s ^ 1);
         ++issued;
       }
     }
-    const int ii = a.tile_inst[tile];
-    const BInst& I = a.inst[ii];
+    const BInst& I = a.inst[dc.inst];
     const int nx = I.nx, ny = I.ny, nt = I.nt;
-    const int lt = tile - I.tile0;
-    const int gx0 = (lt % I.tiles_x) * TX, gy0 = (lt / I.tiles_x) * TY;
+    const int gx0 = dc.gx0, gy0 = dc.gy0;
     const int gx = gx0 + c0;
     const int n = adj ? nt - 1 - step : step;  // the instance's own time index
     const float* cur = (!adj && step == 0) ? I.img : I.P[step & 1];
@@ -89,8 +102,19 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
     const bool compute = adj || n < nt - 1;  // the forward's last index only samples
     float* out = final_step ? const_cast<float*>(I.img) : I.P[(step + 1) & 1];
 
+    const bool load_d = !(!adj && n == 0);
+    float4 d4[RUN];
+    auto load_own_d = [&]() {
+#pragma unroll
+      for (int rr = 0; rr < RUN; ++rr) {
+        const int gy = gy0 + r0 + rr;
+        const bool in = compute && load_d && gy < ny && gx < nx;
+        d4[rr] = in ? ld_stream4(I.D + (long long)gy * nx + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
     if (!adj) {  // y[s, n] = sum_k w_k P^n[cell_k] for the sensors based in this tile
-      for (int e = I.samp_ptr[lt] + t; e < I.samp_ptr[lt + 1]; e += THREADS) {
+      load_own_d();  // independent of the sampling: in flight while it runs
+      for (int e = dc.e0 + t; e < dc.e1; e += THREADS) {
         const int sn = I.samp[e];
         float v = 0.f;
         for (int q = 0; q < I.corners; ++q)
@@ -98,22 +122,16 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
         I.y[(long long)sn * nt + n] = v;
       }
     } else {  // G += S^T r_m on the tile's own cells
-      for (int e = I.inj_ptr[lt] + t; e < I.inj_ptr[lt + 1]; e += THREADS) {
-        const InjCell c = I.inj[e];
-        float v = 0.f;
-        for (int q = c.beg; q < c.end; ++q) v = fmaf(I.ent_w[q], I.y[(long long)I.ent_sensor[q] * nt + n], v);
-        I.D[c.local] += v;
+      if (dc.e1 > dc.e0) {  // uniform over the CTA
+        for (int e = dc.e0 + t; e < dc.e1; e += THREADS) {
+          const InjCell c = I.inj[e];
+          float v = 0.f;
+          for (int q = c.beg; q < c.end; ++q) v = fmaf(I.ent_w[q], I.y[(long long)I.ent_sensor[q] * nt + n], v);
+          I.D[c.local] += v;
+        }
+        __syncthreads();  // the injected cells are read below by other threads of the CTA
       }
-      __syncthreads();  // the injected cells are read below by other threads of the CTA
-    }
-
-    const bool load_d = !(!adj && n == 0);
-    float4 d4[RUN];
-#pragma unroll
-    for (int rr = 0; rr < RUN; ++rr) {
-      const int gy = gy0 + r0 + rr;
-      const bool in = compute && load_d && gy < ny && gx < nx;
-      d4[rr] = in ? ld_stream4(I.D + (long long)gy * nx + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      load_own_d();
     }
     const bool good = mbar_wait(&bars[s], (k >> 1) & 1, a.timeout_ns);
     if (__syncthreads_or(!good)) {
@@ -166,6 +184,8 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
       }
     }
     __syncthreads();  // this stage is refilled by the next iteration's TMA
+    dc = dn;
+    dn = dnn;
   }
   // after a timed-out wait: give the copies in flight a bounded chance to land
   if (t == 0 && !ok)

@@ -136,7 +136,7 @@ struct StepArgs {
 bool persist2d_supported(int R, bool varc);
 int persist2d_tile_x();
 int persist2d_tile_y();
-size_t persist2d_smem_bytes(int R, bool adj);
+size_t persist2d_smem_bytes(int R, bool adj, bool varc);
 size_t persist2d_xbuf_words(int R, bool adj, int ntiles);  // 64-bit exchange words
 int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
