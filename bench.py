@@ -784,7 +784,7 @@ def run_batch(args):
                 "h2d_bytes_per_step": int(sum(y.nbytes for y in y_np)),
                 "d2h_bytes_per_step": int(sum(w.N * 4 for w in ws))},
         # graph nodes per CG iteration; right-hand side (batched K*, fills, E_s*, CG start) and final E_s; L2 flush
-        "gpu_launches": int(args.steps * (iters * info["graph_nodes"] + max_nt + 11 * n_inst + 1)),
+        "gpu_launches": int(args.steps * (iters * info["graph_nodes"] + max_nt + 12 * n_inst + 1)),
         "clocks": clocks,
     }
     if rank == 0:

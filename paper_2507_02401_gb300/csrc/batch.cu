@@ -83,6 +83,8 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     I.img = p->d_img;
     I.P[0] = p->d_wv[0];
     I.P[1] = p->d_wv[1];
+    I.P_lo[0] = p->d_wv[3];
+    I.P_lo[1] = p->d_wv[4];
     I.D = p->d_wv[2];
     I.y = p->d_ybuf;
     I.sens_cell = p->d_sens_cell;
@@ -130,12 +132,12 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     inst[k].samp = ds;
     inst[k].inj = di;
   }
-  std::vector<CUtensorMap> maps(3 * (size_t)B);
+  std::vector<CUtensorMap> maps(BATCH_MAPS * (size_t)B);
   for (int k = 0; k < B; ++k) {
     const BInst& I = inst[k];
-    PAT_TRY_CUDA(batch_encode(I.P[0], I.nx, I.ny, b->R, variant, &maps[3 * k + 0]));
-    PAT_TRY_CUDA(batch_encode(I.P[1], I.nx, I.ny, b->R, variant, &maps[3 * k + 1]));
-    PAT_TRY_CUDA(batch_encode(I.img, I.nx, I.ny, b->R, variant, &maps[3 * k + 2]));
+    const float* fields[BATCH_MAPS] = {I.P[0], I.P[1], I.img, I.P_lo[0], I.P_lo[1]};
+    for (int f = 0; f < BATCH_MAPS; ++f)
+      PAT_TRY_CUDA(batch_encode(fields[f], I.nx, I.ny, b->R, variant, &maps[BATCH_MAPS * k + f]));
   }
   PAT_TRY(balloc(b, &b->d_inst, (size_t)B, "batch instances"));
   PAT_TRY(balloc(b, &b->d_tiles, tiles.size(), "batch tile table"));  // cudaMalloc: 16-byte aligned entries
@@ -146,8 +148,9 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BTile) * tiles.size(), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
-  b->nctas = batch_max_ctas(b->R, variant);
-  if (b->nctas <= 0) {
+  b->nctas = batch_max_ctas(b->R, variant, false);
+  b->nctas_adj = batch_max_ctas(b->R, variant, true);
+  if (b->nctas <= 0 || b->nctas_adj <= 0) {
     set_error("batched step kernel does not fit on this device");
     return PAT_ERR_CUDA;
   }
@@ -179,11 +182,12 @@ pat_status batch_forward(pat_batch* b, cudaStream_t st, int steps = -1) {
 // K* of every instance: the plans' sensor-data buffers -> the plans' image buffers.
 pat_status batch_adjoint(pat_batch* b, cudaStream_t st) {
   for (pat_plan* p : b->plans) {
-    PAT_TRY_CUDA(fill_launch(p->d_wv[0], p->N, 0.f, st));  // Q^{nt} = 0
+    PAT_TRY_CUDA(fill_launch(p->d_wv[0], p->N, 0.f, st));  // Z^{nt} = 0
+    PAT_TRY_CUDA(fill_launch(p->d_wv[3], p->N, 0.f, st));  // Z_lo^{nt} = 0
     PAT_TRY_CUDA(fill_launch(p->d_wv[2], p->N, 0.f, st));  // G = 0
   }
   for (int t = 0; t < b->max_nt; ++t)
-    PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, true), b->nctas, st));
+    PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, true), b->nctas_adj, st));
   return PAT_OK;
 }
 

@@ -15,7 +15,8 @@ struct BInst {
   int ns, corners;
   float kappa0, kappa0_lo;
   const float* img;  // forward input P^0 / adjoint output x (the plan's image buffer)
-  float* P[2];       // ping-pong fields: P^n (forward) or Q^m (adjoint)
+  float* P[2];       // ping-pong fields: P^n (forward) or Z^m = kappa Q^m (adjoint)
+  float* P_lo[2];    // adjoint: ping-pong compensation Z_lo^m
   float* D;          // increment D (forward) or G (adjoint), updated in place
   float* y;          // sensor data: forward output, adjoint input (ns x nt)
   const int* sens_cell;
@@ -38,7 +39,7 @@ struct alignas(16) BTile {
 struct BatchStepArgs {
   const BInst* inst;
   const BTile* tiles;         // tile table
-  const CUtensorMap* maps;    // 3 per instance: P[0], P[1], img (halo boxes)
+  const CUtensorMap* maps;    // BATCH_MAPS per instance: P[0], P[1], img, P_lo[0], P_lo[1] (halo boxes)
   int t;                      // global step: forward n = t, adjoint m = nt - 1 - t
   int adjoint;
   int active;                 // tiles of the instances still running at step t (a prefix of the table)
@@ -47,13 +48,15 @@ struct BatchStepArgs {
   long long timeout_ns;
 };
 
+constexpr int BATCH_MAPS = 5;
+
 // batch.cu: every plan 2D, constant medium, one stencil order, nx % 4 == 0, no plan twice
 bool batch_eligible(pat_plan* const* plans, int B);
 
 // batch_kernels.cu
 int batch_tile_y(int variant);  // tile height of a kernel variant (0: 64 rows, 1: 32 rows)
-size_t batch_smem(int R, int variant);
-int batch_max_ctas(int R, int variant);  // co-resident CTAs on this device
+size_t batch_smem(int R, int variant, bool adj);
+int batch_max_ctas(int R, int variant, bool adj);  // co-resident CTAs on this device
 cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st);
 cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map);
 
@@ -62,7 +65,7 @@ cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, 
 struct pat_batch {
   std::vector<pat_plan*> plans;  // borrowed, in the caller's order
   std::vector<int> order;        // instance slots sorted by nt, longest first (slot -> caller index)
-  int B = 0, R = 1, variant = 0, nctas = 0, max_nt = 0, ntiles = 0;
+  int B = 0, R = 1, variant = 0, nctas = 0, nctas_adj = 0, max_nt = 0, ntiles = 0;
   std::vector<int> active;       // active[t]: tiles still running at global step t
   pat::BInst* d_inst = nullptr;
   pat::BTile* d_tiles = nullptr;

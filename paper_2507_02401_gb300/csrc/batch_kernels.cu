@@ -1,27 +1,32 @@
 // Batched 2D step kernel: one launch advances every running instance of a
 // batch by one time step of the increment form (paper Sec. 2, Eq.
-// wave_equation, eliminated to p only; constant medium, so the adjoint has
-// the same recurrence):
+// wave_equation, eliminated to p only; constant medium):
 //
 //   forward, n = t:          D <- D + c_lap kappa L P^n,   P^{n+1} = P^n + D,   y[., n] = S P^n
-//   adjoint, m = nt - 1 - t: G <- G + S^T r_m + kappa L Q^{m+1},  Q^m = Q^{m+1} + G
-//                            (m = 0: x = G + 1/2 kappa L Q^1)
+//   adjoint, m = nt - 1 - t: G <- G + S^T r_m + c_lap L Z^{m+1},  Z^m = Z^{m+1} + kappa G
+//                            (Z = kappa Q; m = 0: x = G + 1/2 L Z^1)
+//
+// The adjoint state Z integrates G over time and, in a closed box, grows far
+// beyond the result: it is kept as a compensated pair Z + Z_lo (TwoSum), the
+// stencil sees Z through the difference form and Z_lo through the pair form,
+// as in the single-instance 2D step kernel.
 //
 // The tiles (64 columns x 64 or 32 rows) of all instances form one table,
 // instances ordered by their number of time samples (longest first), so the
 // tiles still running at global step t are a prefix of the table.  Persistent
 // CTAs walk that prefix with the tile pipeline of the single-instance 2D step
-// kernel: TMA halo boxes of P in two shared-memory stages, D in registers, a
-// sliding y window per thread.  Sampling and injection are fused per tile
-// (each tile samples the sensors whose base cell it holds and injects into
-// its own cells).  Each tile's descriptor (instance, origin, list ranges) is
-// read two tiles ahead of its use, so the only loads left between the end of
-// one tile and the stencil of the next are the tile's own D cells and the
-// TMA box issued one tile ahead.
+// kernel: TMA halo boxes (P, or Z and Z_lo) in two shared-memory stages, D / G
+// in registers, a sliding y window per thread.  Sampling and injection are
+// fused per tile (each tile samples the sensors whose base cell it holds and
+// injects into its own cells).  Each tile's descriptor (instance, origin, list
+// ranges) is read two tiles ahead of its use, so the only loads left between
+// the end of one tile and the stencil of the next are the tile's own D cells
+// and the TMA boxes issued one tile ahead.
 #include <mutex>
 
 #include "batch.h"
 #include "stencil.cuh"
+#include "tile2d.cuh"
 #include "tma.cuh"
 
 namespace pat {
@@ -29,25 +34,25 @@ namespace {
 
 constexpr int TX = 64, RUN = 8, XH = 8, BW = TX + 2 * XH;
 
-template <int R, int TY>
+template <int R, int TY, bool ADJ>
 struct GB {
   static constexpr int THREADS = (TX / 4) * (TY / RUN);
   static constexpr int PBOX = BW * (TY + 2 * R);  // floats (multiple of 32: 128-byte aligned stages)
-  static constexpr size_t SMEM = sizeof(float) * 2 * PBOX + 16;
+  static constexpr int STAGE = (ADJ ? 2 : 1) * PBOX;
+  static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
 };
 
-template <int R, int TY>
-__global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const BatchStepArgs a) {
-  using G = GB<R, TY>;
+template <int R, int TY, bool ADJ>
+__global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(const BatchStepArgs a) {
+  using G = GB<R, TY, ADJ>;
   constexpr int THREADS = G::THREADS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::PBOX);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
 
   const int t = threadIdx.x;
   const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * RUN;
   const int step = a.t;
-  const bool adj = a.adjoint != 0;
 
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -66,15 +71,17 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
     if (tile < a.active) {
       const int4* p = reinterpret_cast<const int4*>(a.tiles + tile);
       const int4 u = __ldg(p), v = __ldg(p + 1);
-      d = Desc{u.x, u.y, u.z, adj ? v.z : v.x, adj ? v.w : v.y};
+      d = Desc{u.x, u.y, u.z, ADJ ? v.z : v.x, ADJ ? v.w : v.y};
     }
     return d;
   };
-  // halo box of the field the tile's stencil reads at this step
+  // halo boxes of the fields the tile's stencil reads at this step
   auto issue = [&](const Desc& d, int s) {
-    const CUtensorMap* map = a.maps + 3 * d.inst + ((!adj && step == 0) ? 2 : (step & 1));
-    mbar_expect_tx(&bars[s], (unsigned)G::PBOX * 4u);
-    tma_load_2d(stage0 + s * G::PBOX, map, d.gx0 - XH, d.gy0 - R, &bars[s]);
+    const CUtensorMap* maps = a.maps + BATCH_MAPS * d.inst;
+    float* st = stage0 + s * G::STAGE;
+    mbar_expect_tx(&bars[s], (unsigned)G::STAGE * 4u);
+    tma_load_2d(st, maps + ((!ADJ && step == 0) ? 2 : (step & 1)), d.gx0 - XH, d.gy0 - R, &bars[s]);
+    if (ADJ) tma_load_2d(st + G::PBOX, maps + 3 + (step & 1), d.gx0 - XH, d.gy0 - R, &bars[s]);
   };
   Desc dc = desc(blockIdx.x), dn = desc(blockIdx.x + gridDim.x);
   if (t == 0 && (int)blockIdx.x < a.active) issue(dc, 0);
@@ -96,13 +103,13 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
     const int nx = I.nx, ny = I.ny, nt = I.nt;
     const int gx0 = dc.gx0, gy0 = dc.gy0;
     const int gx = gx0 + c0;
-    const int n = adj ? nt - 1 - step : step;  // the instance's own time index
-    const float* cur = (!adj && step == 0) ? I.img : I.P[step & 1];
-    const bool final_step = adj && n == 0;
-    const bool compute = adj || n < nt - 1;  // the forward's last index only samples
+    const int n = ADJ ? nt - 1 - step : step;  // the instance's own time index
+    const float* cur = (!ADJ && step == 0) ? I.img : I.P[step & 1];
+    const bool final_step = ADJ && n == 0;
+    const bool compute = ADJ || n < nt - 1;  // the forward's last index only samples
     float* out = final_step ? const_cast<float*>(I.img) : I.P[(step + 1) & 1];
 
-    const bool load_d = !(!adj && n == 0);
+    const bool load_d = !(!ADJ && n == 0);
     float4 d4[RUN];
     auto load_own_d = [&]() {
 #pragma unroll
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
         d4[rr] = in ? ld_stream4(I.D + (long long)gy * nx + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    if (!adj) {  // y[s, n] = sum_k w_k P^n[cell_k] for the sensors based in this tile
+    if (!ADJ) {  // y[s, n] = sum_k w_k P^n[cell_k] for the sensors based in this tile
       load_own_d();  // independent of the sampling: in flight while it runs
       for (int e = dc.e0 + t; e < dc.e1; e += THREADS) {
         const int sn = I.samp[e];
@@ -133,6 +140,7 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
       }
       load_own_d();
     }
+
     const bool good = mbar_wait(&bars[s], (k >> 1) & 1, a.timeout_ns);
     if (__syncthreads_or(!good)) {
       if (t == 0) atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -140,9 +148,12 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
       break;
     }
     if (compute) {
-      const float* P = stage0 + s * G::PBOX;
+      const float* P = stage0 + s * G::STAGE;  // P (forward) or Z (adjoint)
+      const float* PL = P + G::PBOX;           // adjoint: Z_lo
       const float c_lap = (n == 0 || final_step) ? 0.5f : 1.f;
       const float ckh = c_lap * I.kappa0, ckl = c_lap * I.kappa0_lo;
+      float lo[RUN][4];  // adjoint: the Z_lo part of the stencil, first pass
+      if (ADJ) stencil_run<R, RUN, BW, XH>(PL, r0, c0, a.w, lo);
       float4 win[2 * R + 1];
 #pragma unroll
       for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(P + (r0 + i) * BW + XH + c0);
@@ -151,33 +162,35 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
         win[2 * R] = *reinterpret_cast<const float4*>(P + (r0 + rr + 2 * R) * BW + XH + c0);
         const int brow = r0 + rr + R;
         float f[20];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const float4 v = *reinterpret_cast<const float4*>(P + brow * BW + c0 + 4 * q);
-          f[4 * q + 0] = v.x;
-          f[4 * q + 1] = v.y;
-          f[4 * q + 2] = v.z;
-          f[4 * q + 3] = v.w;
-        }
-        float dn[4], pn[4];
+        load_row20(P + brow * BW + c0, f);
+        float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ADJ) zl4 = *reinterpret_cast<const float4*>(PL + brow * BW + XH + c0);
+        float dn[4], pn[4], pl[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float c = f[8 + j];
-          const float c2 = c + c;
-          float acc = 0.f;  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
-#pragma unroll
-          for (int m = 1; m <= R; ++m)
-            acc = fmaf(a.w[m], pair_term<false>(f4get(win[R + m], j), f4get(win[R - m], j), c, c2), acc);
-#pragma unroll
-          for (int m = 1; m <= R; ++m) acc = fmaf(a.w[m], pair_term<false>(f[8 + j + m], f[8 + j - m], c, c2), acc);
-          dn[j] = f4get(d4[rr], j) + fmaf(ckh, acc, ckl * acc);
-          pn[j] = final_step ? dn[j] : c + dn[j];
+          if (!ADJ) {  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
+            const float acc = stencil_cell<R, false>(win, f, j, a.w);
+            dn[j] = f4get(d4[rr], j) + fmaf(ckh, acc, ckl * acc);
+            pn[j] = c + dn[j];
+            pl[j] = 0.f;
+          } else {
+            const float acc = stencil_cell<R, true>(win, f, j, a.w) + lo[rr][j];
+            const float g = fmaf(c_lap, acc, f4get(d4[rr], j));
+            dn[j] = g;
+            float e = 0.f;
+            pn[j] = final_step ? g : two_sum(c, fmaf(I.kappa0, g, I.kappa0_lo * g), e);  // Z += kappa G
+            pl[j] = f4get(zl4, j) + e;
+          }
         }
         const int gy = gy0 + r0 + rr;
         if (gy < ny && gx < nx) {
           const long long gi = (long long)gy * nx + gx;
           *reinterpret_cast<float4*>(out + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-          if (!final_step) *reinterpret_cast<float4*>(I.D + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+          if (!final_step) {
+            *reinterpret_cast<float4*>(I.D + gi) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+            if (ADJ) *reinterpret_cast<float4*>(I.P_lo[(step + 1) & 1] + gi) = make_float4(pl[0], pl[1], pl[2], pl[3]);
+          }
         }
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
@@ -193,17 +206,18 @@ __global__ void __launch_bounds__(GB<R, TY>::THREADS) batch_step_kernel(const Ba
 }
 
 template <int R, int TY>
-const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&batch_step_kernel<R, TY>);
+const void* kernel_ptr(bool adj) {
+  return adj ? reinterpret_cast<const void*>(&batch_step_kernel<R, TY, true>)
+             : reinterpret_cast<const void*>(&batch_step_kernel<R, TY, false>);
 }
 
-const void* kernel_for(int R, int variant) {
+const void* kernel_for(int R, int variant, bool adj) {
   const bool tall = variant == 0;
   switch (R) {
-    case 1: return tall ? kernel_ptr<1, 64>() : kernel_ptr<1, 32>();
-    case 3: return tall ? kernel_ptr<3, 64>() : kernel_ptr<3, 32>();
-    case 5: return tall ? kernel_ptr<5, 64>() : kernel_ptr<5, 32>();
-    case 7: return tall ? kernel_ptr<7, 64>() : kernel_ptr<7, 32>();
+    case 1: return tall ? kernel_ptr<1, 64>(adj) : kernel_ptr<1, 32>(adj);
+    case 3: return tall ? kernel_ptr<3, 64>(adj) : kernel_ptr<3, 32>(adj);
+    case 5: return tall ? kernel_ptr<5, 64>(adj) : kernel_ptr<5, 32>(adj);
+    case 7: return tall ? kernel_ptr<7, 64>(adj) : kernel_ptr<7, 32>(adj);
     default: return nullptr;
   }
 }
@@ -214,14 +228,14 @@ int threads_for(int variant) { return (TX / 4) * (batch_tile_y(variant) / RUN); 
 
 int batch_tile_y(int variant) { return variant == 0 ? 64 : 32; }
 
-size_t batch_smem(int R, int variant) {
-  return sizeof(float) * 2 * (size_t)BW * (batch_tile_y(variant) + 2 * R) + 16;
+size_t batch_smem(int R, int variant, bool adj) {
+  return sizeof(float) * 2 * (adj ? 2 : 1) * (size_t)BW * (batch_tile_y(variant) + 2 * R) + 16;
 }
 
-int batch_max_ctas(int R, int variant) {
-  const void* fn = kernel_for(R, variant);
+int batch_max_ctas(int R, int variant, bool adj) {
+  const void* fn = kernel_for(R, variant, adj);
   if (!fn) return 0;
-  const size_t smem = batch_smem(R, variant);
+  const size_t smem = batch_smem(R, variant, adj);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -238,11 +252,12 @@ int batch_max_ctas(int R, int variant) {
 
 cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st) {
   if (a.active <= 0) return cudaSuccess;
-  const void* fn = kernel_for(R, variant);
+  const bool adj = a.adjoint != 0;
+  const void* fn = kernel_for(R, variant, adj);
   if (!fn) return cudaErrorInvalidValue;
   const int grid = nctas < a.active ? nctas : a.active;
   void* args[] = {const_cast<BatchStepArgs*>(&a)};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant)), args, batch_smem(R, variant), st);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant)), args, batch_smem(R, variant, adj), st);
 }
 
 cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map) {

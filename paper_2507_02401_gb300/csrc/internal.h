@@ -136,7 +136,7 @@ struct StepArgs {
 bool persist2d_supported(int R, bool varc);
 int persist2d_tile_x();
 int persist2d_tile_y();
-size_t persist2d_smem_bytes(int R, bool adj, bool varc);
+size_t persist2d_smem_bytes(int R, bool adj);
 size_t persist2d_xbuf_words(int R, bool adj, int ntiles);  // 64-bit exchange words
 int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
@@ -172,8 +172,9 @@ cudaError_t sample_launch(const float* P, int ns, int nt, int t, const int* cell
                           float* y, cudaStream_t st);
 cudaError_t inject_launch(float* Q, int n_inj, const int* inj_cell, const int* inj_ptr, const int* ent_sensor,
                           const float* ent_w, const float* r, int nt, int t, float scale, cudaStream_t st);
+// zform: the adjoint state holds Z = kappa Q (2D TMA engine); the accumulator divides by kappa
 cudaError_t grad_acc_launch(int R, double* gacc, const float* Q, const float* Qlo, const float* P, float coef,
-                            const StepArgs& a, int dim, cudaStream_t st);
+                            const StepArgs& a, int dim, bool zform, cudaStream_t st);
 cudaError_t d2f_launch(float* out, const double* in, long long n, cudaStream_t st);
 cudaError_t dfill_launch(double* p, long long n, cudaStream_t st);
 cudaError_t fill_launch(float* p, long long n, float v, cudaStream_t st);

@@ -91,7 +91,7 @@ static const pat_plan::TmaDesc* tma_desc(pat_plan* p, const float* base) {
 // The TMA kernels take 16-byte aligned fields (descriptor bases, float4 stores).
 static bool tma_ready(pat_plan* p, const StepArgs& a) {
   auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
-  return al(a.cur) && al(a.prev) && al(a.next) && (p->dim == 3 || al(a.dbuf));
+  return al(a.cur) && al(a.prev) && al(a.next) && (p->dim == 3 || (al(a.dbuf) && al(a.cur_lo) && al(a.next_lo)));
 }
 
 static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t st) {
@@ -99,32 +99,31 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
   float* y = a.y;
   cudaError_t e;
   if (p->dim == 2 && p->tma2d && tma_ready(p, a)) {
-    // TMA tile pipelines: forward; constant-medium adjoint (same recurrence); varying-medium adjoint
-    // with kappa Q formed in shared memory
-    const bool varc = p->varc && !adj;
-    // injection fused for radius <= 3; at radius 5-7 the fused variant's code generation is slower than
-    // mode 0 plus a separate injection launch on every grid measured (2048^2 .. 16384^2)
-    const bool fuse = a.inj_r && p->R <= 3 && !p->varc;
-    const int mode = varc ? 1 : (adj && p->varc ? 3 : (fuse ? 2 : 0));
+    // TMA tile pipelines: forward (constant or varying medium); adjoint in Z = kappa Q with Z
+    // compensated (boxes of Z and Z_lo), its injection S^T r_m added to G by a launch just before
+    const int mode = adj ? 2 : (p->varc ? 1 : 0);
     const int sp = p->sponge_w > 0 ? (adj ? 2 : 1) : 0;
     const long long nthr = tma2d_threads(p->n[0], p->n[1], p->R, mode, sp);
     if (y && a.ns > nthr) a.y = nullptr;
+    // copies: a second lookup may move the cached descriptors
     const pat_plan::TmaDesc* dp = tma_desc(p, a.cur);
     if (!dp) return cudaErrorInvalidValue;
+    const CUtensorMap mcur = dp->halo;
+    CUtensorMap mlo = mcur;
+    if (adj) {
+      const pat_plan::TmaDesc* dl = tma_desc(p, a.cur_lo);
+      if (!dl) return cudaErrorInvalidValue;
+      mlo = dl->halo;
+    }
     StepArgs b = a;
-    if (!varc) b.kappa = b.kappa_lo = nullptr;
-    if (fuse) {  // injection fused per tile
-      b.inj_tile_ptr = p->d_tinj2_ptr;
-      b.inj_tile = p->d_tinj2;
-      b.ent_sensor = p->d_ent_sensor;
-      b.ent_w = p->d_ent_w;
-    } else if (a.inj_r) {
+    if (!p->varc) b.kappa = b.kappa_lo = nullptr;
+    if (a.inj_r) {
       e = inject_launch(a.dbuf, p->n_inj, p->d_inj_cell, p->d_inj_ptr, p->d_ent_sensor, p->d_ent_w, a.inj_r, p->nt,
                         a.inj_t, 1.f, st);
       if (e != cudaSuccess) return e;
       b.inj_r = nullptr;
     }
-    e = step2d_tma_launch(p->R, mode, sp, b, dp->halo, p->tma_kappa, p->d_status, p->timeout_ns, st);
+    e = step2d_tma_launch(p->R, mode, sp, b, mcur, mlo, p->d_status, p->timeout_ns, st);
   } else if (p->dim == 2) {
     const long long nthr = (long long)((p->n[0] + 63) / 64) * ((p->n[1] + 31) / 32) * 256;
     if (y && a.ns > nthr) a.y = nullptr;
@@ -240,7 +239,10 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
   a.y = nullptr;
   if (p->dim == 2) {
     // increment form with compensation: G = wv[2] (+ wv[5]); Q^m in wv[(nt-m) % 2]
-    // (+ wv[3 + (nt-m) % 2]) with Q^nt = 0
+    // (+ wv[3 + (nt-m) % 2]) with Q^nt = 0.  The TMA kernel keeps Z = kappa Q there (and no G_lo);
+    // the plain kernel Q itself, so every step of one application runs on the same kernel: with
+    // the TMA kernel an output that is not 16-byte aligned is written to a free field buffer
+    // (Q^2's, no longer read by the final step) and copied.
     float* G = p->d_wv[2];
     auto Qbuf = [&](int m) { return p->d_wv[(nt - m) % 2]; };
     auto Qlo = [&](int m) { return p->d_wv[3 + (nt - m) % 2]; };
@@ -265,11 +267,13 @@ static pat_status wave_adjoint_impl(pat_plan* p, const float* y, float* x, cudaS
     a.inj_t = 0;
     a.cur = Qbuf(1);
     a.cur_lo = Qlo(1);
-    a.next = x;
+    const bool staged = p->tma2d && ((uintptr_t)x & 15) != 0;
+    a.next = staged ? Qbuf(2) : x;
     a.next_lo = nullptr;
     a.final_step = 1;
     a.c_lap = 0.5f;
     PAT_TRY_CUDA(step_launch(p, true, a, st));
+    if (staged) PAT_TRY_CUDA(cudaMemcpyAsync(x, Qbuf(2), sizeof(float) * p->N, cudaMemcpyDeviceToDevice, st));
     return PAT_OK;
   }
   // three-level form: Q^m lives in wv[(nt-1-m) % 3]
@@ -315,7 +319,6 @@ static long long wave_kernels(const pat_plan* p, bool adj) {
   if (nt == 1) return adj ? 2 : 1;
   if (!adj) return nt;  // nt-1 steps + final sample
   const long long inj = p->n_inj > 0 ? 1 : 0;
-  if (p->dim == 2 && p->tma2d && !p->varc && p->R <= 3) return 4 + (nt - 1) + 1;  // 4 fills, fused injection
   if (p->dim == 2) return 4 + (nt - 1) * (1 + inj) + (1 + inj);  // 4 fills, (inject+step) x (nt-1), final
   if (p->tma3d) return (1 + inj) + (nt - 2) + 1;                   // fill+inject, steps with fused injection
   return (1 + inj) + (nt - 2) * (1 + inj) + (1 + inj);             // fill+inject, (step+inject), final
@@ -569,7 +572,8 @@ pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float*
   auto accumulate = [&](int m, const float* Q, const float* Qlo) -> pat_status {
     const int n = m - 1;
     if (n / C != loaded) PAT_TRY(load_segment(n / C));
-    PAT_TRY_CUDA(grad_acc_launch(p->R, p->kg_acc, Q, Qlo, seg(n - loaded * C), n == 0 ? 0.5f : 1.f, a, p->dim, st));
+    PAT_TRY_CUDA(grad_acc_launch(p->R, p->kg_acc, Q, Qlo, seg(n - loaded * C), n == 0 ? 0.5f : 1.f, a, p->dim,
+                                 two_d && p->tma2d, st));
     return PAT_OK;
   };
   PAT_TRY_CUDA(dfill_launch(p->kg_acc, N, st));

@@ -473,31 +473,7 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   if (p->dim == 2 && tma2d_supported(p->n[0], p->R) && !(env2 && strcmp(env2, "plain") == 0)) {
     CUtensorMap mh, mo;
     if (tma2d_encode(p->d_wv[0], p->n[0], p->n[1], p->R, &mh, &mo) == cudaSuccess) p->tma2d = true;
-    if (p->tma2d && p->varc && tma2d_encode(p->d_kappa, p->n[0], p->n[1], p->R, &p->tma_kappa, &mo) != cudaSuccess)
-      p->tma2d = false;
   }
-  if (p->tma2d) {  // injection lists per 64 x 64 tile for the fused adjoint injection (tile-local cells)
-    const int tx = (p->n[0] + 63) / 64, ntl = tx * ((p->n[1] + 63) / 64);
-    std::vector<std::vector<InjCell>> bins(ntl);
-    for (int i = 0; i < p->n_inj; ++i) {
-      const int c = p->h_inj_cell[i];
-      const int cy = c / p->n[0], cx = c % p->n[0];
-      bins[(cy / 64) * tx + cx / 64].push_back(InjCell{(cy % 64) * 64 + cx % 64, p->h_inj_ptr[i], p->h_inj_ptr[i + 1]});
-    }
-    std::vector<int> ptr(1, 0);
-    std::vector<InjCell> cells;
-    for (auto& b : bins) {
-      cells.insert(cells.end(), b.begin(), b.end());
-      ptr.push_back((int)cells.size());
-    }
-    PAT_TRY(alloc_n(p, &p->d_tinj2_ptr, ptr.size(), "tile injection lists"));
-    PAT_TRY(alloc_n(p, &p->d_tinj2, std::max<size_t>(cells.size(), 1), "tile injection lists"));
-    PAT_TRY_CUDA(cudaMemcpyAsync(p->d_tinj2_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st));
-    if (!cells.empty())
-      PAT_TRY_CUDA(cudaMemcpyAsync(p->d_tinj2, cells.data(), sizeof(InjCell) * cells.size(), cudaMemcpyHostToDevice,
-                                   st));
-  }
-
   // 3D constant media: TMA plane pipelines when the driver can encode the descriptors
   p->tma3d = false;
   const char* env3 = getenv("PAT_STEP3D");

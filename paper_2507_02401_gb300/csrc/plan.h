@@ -61,11 +61,8 @@ struct pat_plan {
   bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
   int tma3d_zchunk = 0;
   bool tma2d = false;  // 2D steps through the TMA tile-pipeline kernel (where it applies)
-  CUtensorMap tma_kappa;  // kappa's halo-box descriptor (varying-medium adjoint on that kernel)
   int* d_tinj3_ptr = nullptr;       // 3D TMA kernel: injection lists per CTA (64 x 16 columns x z chunk)
   pat::InjCell* d_tinj3 = nullptr;  // .local = linear cell index
-  int* d_tinj2_ptr = nullptr;       // its per-tile injection lists (64 x 64 tiles)
-  pat::InjCell* d_tinj2 = nullptr;  // .local = ly * 64 + lx within the tile
   struct TmaDesc {
     const float* base;
     CUtensorMap halo, own;  // stencil-input boxes with halo, own-tile boxes

@@ -18,14 +18,9 @@
 // with a constant medium a rounded kappa is the same everywhere and shifts
 // the phase of every mode coherently, step after step.  In the adjoint the
 // state Q integrates G over time and, in a closed (reflecting) box, grows an
-// order of magnitude beyond the result.  With a constant medium G and Q are
-// kept as compensated pairs (TwoSum) and the stencil receives kappa*Q as a
-// hi + lo pair of FP32 fields (hi through the difference-form stencil, lo
-// through the cheap form).  With a varying medium the adjoint exchanges
-// W = (kappa_hi + kappa_lo) Q rounded once and runs uncompensated: FP32
-// emulation of the 512^2, 1500-step, order-8 varying-medium adjoint gave
-// 2.4e-6 (uncompensated) against 1.5e-6 (compensated), while the compensated
-// step costs a second stencil and a second shared-memory field.
+// order of magnitude beyond the result, so G and Q are kept as compensated
+// pairs (TwoSum) and the stencil receives kappa*Q as a hi + lo pair of FP32
+// fields (hi through the difference-form stencil, lo through the cheap form).
 //
 // GB300 mapping.  The grid is cut into 64 x 32 tiles, one CTA per tile, all
 // co-resident (cooperative launch).  Each thread keeps its 2 x 4 cells' state
@@ -55,10 +50,9 @@ constexpr int PITCH = TX + 16;                  // 8 halo columns each side
 constexpr int RCOUNT = NTHREADS / 4;            // threads serving one neighbour
 static_assert(NTHREADS % 128 == 0, "four halo regions need whole warps");
 
-// PAIR: the exchanged state is a compensated (hi, lo) pair (constant-medium adjoint)
-template <int R, bool PAIR>
+template <int R, bool ADJ>
 struct Geo {
-  static constexpr int NF = PAIR ? 2 : 1;          // shared-memory fields: P, or (W_hi, W_lo)
+  static constexpr int NF = ADJ ? 2 : 1;           // shared-memory fields: P, or (W_hi, W_lo)
   static constexpr int ROWS = TY + 2 * R;
   static constexpr int SBUF = ROWS * PITCH;        // one shared-memory field buffer
   static constexpr int STRIP = 2 * R * (TX + TY);  // exchanged words per tile per slot
@@ -71,21 +65,20 @@ struct Geo {
 
 // Exchange words.  The buffer is filled with 0xff bytes before every launch,
 // so no stale word can carry a valid tag.
-//   one field (forward P, varying-medium adjoint W): [step (32 bits)][value (32 bits)]
-//   pair (constant-medium adjoint):
-//            [W_lo with its low 8 mantissa bits replaced by step mod 128][W_hi]
+//   forward: [step (32 bits)][P (32 bits)]
+//   adjoint: [W_lo with its low 8 mantissa bits replaced by step mod 128][W_hi]
 //            (W_lo is a correction ~2^-24 of W_hi; dropping 8 of its bits is
 //            far below FP32 rounding of W)
-template <bool PAIR>
+template <bool ADJ>
 __device__ __forceinline__ u64 pack(float hi, float lo, unsigned step) {
-  if (!PAIR) return ((u64)step << 32) | (u64)__float_as_uint(hi);
+  if (!ADJ) return ((u64)step << 32) | (u64)__float_as_uint(hi);
   const unsigned l = (__float_as_uint(lo) & ~0xffu) | (step & 0x7fu);
   return ((u64)l << 32) | (u64)__float_as_uint(hi);
 }
-template <bool PAIR>
+template <bool ADJ>
 __device__ __forceinline__ bool tag_ok(u64 w, unsigned step) {
   const unsigned h = (unsigned)(w >> 32);
-  return PAIR ? (h & 0xffu) == (step & 0x7fu) : h == step;
+  return ADJ ? (h & 0xffu) == (step & 0x7fu) : h == step;
 }
 __device__ __forceinline__ float word_hi(u64 w) { return __uint_as_float((unsigned)(w & 0xffffffffull)); }
 __device__ __forceinline__ float word_lo(u64 w) { return __uint_as_float((unsigned)(w >> 32) & ~0xffu); }
@@ -115,21 +108,21 @@ __device__ __forceinline__ u64 ld_word(const u64* p) {
 // buffer(s) Sn (second field at Sn + SBUF) and, packed and tagged, into the
 // shared outbox O laid out like the boundary strips:
 // [top R x TX][bottom R x TX][left TY x R][right TY x R].
-template <int R, bool PAIR>
+template <int R, bool ADJ>
 __device__ __forceinline__ void store_state(float* Sn, u64* O, const float V[2][4], const float Vl[2][4], int r0,
                                             int c0, unsigned step) {
-  constexpr int SBUF = Geo<R, PAIR>::SBUF;
+  constexpr int SBUF = Geo<R, ADJ>::SBUF;
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr) {
     const int row = r0 + rr;
     *reinterpret_cast<float4*>(Sn + (row + R) * PITCH + XOFF + c0) =
         make_float4(V[rr][0], V[rr][1], V[rr][2], V[rr][3]);
-    if (PAIR)
+    if (ADJ)
       *reinterpret_cast<float4*>(Sn + SBUF + (row + R) * PITCH + XOFF + c0) =
           make_float4(Vl[rr][0], Vl[rr][1], Vl[rr][2], Vl[rr][3]);
     u64 w[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = pack<PAIR>(V[rr][j], Vl[rr][j], step);
+    for (int j = 0; j < 4; ++j) w[j] = pack<ADJ>(V[rr][j], Vl[rr][j], step);
     u64* dst = nullptr;
     if (row < R) dst = O + row * TX + c0;
     if (row >= TY - R) dst = O + R * TX + (row - (TY - R)) * TX + c0;
@@ -172,10 +165,10 @@ __device__ __forceinline__ void publish_warp(u64* X, const u64* O, int warp, int
 // Copy the halo of state `step` from the neighbour's strips X into the shared
 // buffers at Sc (second field at Sc + SBUF).  Executed by the RCOUNT threads
 // of one region; returns false if the wait ran out.
-template <int R, bool PAIR>
+template <int R, bool ADJ>
 __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsigned step, const int* abort,
                           long long timeout_ns, int poll_ns) {
-  using G = Geo<R, PAIR>;
+  using G = Geo<R, ADJ>;
   const bool ns = region < 2;
   const int per = ns ? G::PER_NS : G::PER_WE;
   const int count = ns ? G::NPAIR : G::NSIDE;
@@ -191,20 +184,20 @@ __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsign
       if (ns) {
         u64 a, b;
         ld_word2(X + (region == 0 ? R * TX : 0) + 2 * i, a, b);
-        if (tag_ok<PAIR>(a, step) && tag_ok<PAIR>(b, step)) {
+        if (tag_ok<ADJ>(a, step) && tag_ok<ADJ>(b, step)) {
           const int row = (2 * i) / TX, col = (2 * i) % TX;
           const int o = (region == 0 ? row : TY + R + row) * PITCH + XOFF + col;
           *reinterpret_cast<float2*>(Sc + o) = make_float2(word_hi(a), word_hi(b));
-          if (PAIR) *reinterpret_cast<float2*>(Sc + G::SBUF + o) = make_float2(word_lo(a), word_lo(b));
+          if (ADJ) *reinterpret_cast<float2*>(Sc + G::SBUF + o) = make_float2(word_lo(a), word_lo(b));
           pending &= ~bit;
         }
       } else {
         const u64 a = ld_word(X + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
-        if (tag_ok<PAIR>(a, step)) {
+        if (tag_ok<ADJ>(a, step)) {
           const int row = i / R, jj = i % R;
           const int o = (row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj);
           Sc[o] = word_hi(a);
-          if (PAIR) Sc[G::SBUF + o] = word_lo(a);
+          if (ADJ) Sc[G::SBUF + o] = word_lo(a);
           pending &= ~bit;
         }
       }
@@ -226,8 +219,7 @@ __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsign
 //   compensation terms are carried approximately (the fields are being damped there).
 template <int R, bool ADJ, bool VARC, bool SP>
 __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persist2DArgs a) {
-  constexpr bool PAIR = ADJ && !VARC;
-  using G = Geo<R, PAIR>;
+  using G = Geo<R, ADJ>;
   extern __shared__ float4 smem4[];
   float* S0 = reinterpret_cast<float*>(smem4);  // [slot][field] buffers
   float* J0 = S0 + 2 * G::NF * G::SBUF;         // adjoint injection accumulators, 2 x TY x TX
@@ -255,7 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   if (region == 2 && tix > 0) nb = tile - 1;
   if (region == 3 && tix < a.tiles_x - 1) nb = tile + 1;
 
-  // forward: P, D ; adjoint: Q (in P), G (in D) and (PAIR) their compensation terms
+  // forward: P, D ; adjoint: Q (in P), G (in D) and their compensation terms
   float P[2][4], D[2][4], K[2][4];
   float Pl[2][4], Dl[2][4], Kl[2][4];
   float SA[2][4], SB[2][4];  // layer factors (SP only)
@@ -284,15 +276,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   __syncthreads();
 
   {  // publish state 0 (forward: x; adjoint: zero)
-    store_state<R, PAIR>(S0, OB, P, Pl, r0, c0, 0u);
+    store_state<R, ADJ>(S0, OB, P, Pl, r0, c0, 0u);
     publish_warp<R>(xbuf + (size_t)tile * 2 * G::SLOT, OB, warp, lane);
   }
 
   for (int k = 0; k < nt; ++k) {
     float* Sc = S0 + (k & 1) * G::NF * G::SBUF;
     float* Jc = J0 + (k & 1) * TX * TY;
-    if (ADJ) {  // S^T r_n for this tile's injected cells, n = nt-1-k (the data does not depend on the
-                //  halo: its dependent loads overlap the neighbours' exchange)
+    if (ADJ) {  // S^T r_n for this tile's injected cells, n = nt-1-k (independent of the halo: these
+                //  dependent loads overlap the neighbours' exchange)
       const int n = nt - 1 - k;
       const int e1 = a.tile_inj_ptr[tile + 1];
       for (int e = a.tile_inj_ptr[tile] + t; e < e1; e += NTHREADS) {
@@ -305,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
     // ---- halo of state k from the neighbour's slot (k & 1)
     if (nb >= 0) {
       const u64* X = xbuf + ((size_t)nb * 2 + (k & 1)) * G::SLOT;
-      if (!load_halo<R, PAIR>(Sc, X, region, rrank, (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
+      if (!load_halo<R, ADJ>(Sc, X, region, rrank, (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
         if (lane == 0) {
           s_abort = 1;
           atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -332,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
 
     float L[2][4];
     lap_2x4<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, a.w, L);
-    if (PAIR) lap_2x4<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, a.w, L);
+    if (ADJ) lap_2x4<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, a.w, L);
 
     if (k == nt - 1) {
       if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L(kappa Q^1)
@@ -376,17 +368,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
           const int li = (r0 + rr) * TX + c0 + j;
           const float inc = Jc[li] + L[rr][j];
           Jc[li] = 0.f;
-          if (!PAIR) {  // varying medium: G += inc, Q += G (Q = a Q + b G in the layer), W = kappa Q
-            float g = D[rr][j] + inc;
-            float q = (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) ? fmaf(SA[rr][j], P[rr][j], SB[rr][j] * g)
-                                                                     : P[rr][j] + g;
-            if (!valid[rr][j]) g = q = 0.f;
-            D[rr][j] = g;
-            P[rr][j] = q;
-            V[rr][j] = fmaf(K[rr][j], q, Kl[rr][j] * q);
-            Vl[rr][j] = 0.f;
-            continue;
-          }
           float e;
           float g = two_sum(D[rr][j], inc + Dl[rr][j], e);  // G += inc (compensated)
           float gl = e;
@@ -413,7 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
     u64* On = OB + ((k + 1) & 1) * G::SLOT;
     if (lane == 0) bulk_wait_read_1();  // the copy that last read this outbox half is done
     __syncwarp();
-    store_state<R, PAIR>(Sn, On, V, Vl, r0, c0, (unsigned)(k + 1));
+    store_state<R, ADJ>(Sn, On, V, Vl, r0, c0, (unsigned)(k + 1));
     publish_warp<R>(xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT, On, warp, lane);
   }
   if (lane == 0) bulk_wait_all();
@@ -451,15 +432,15 @@ void* pick_sp(int R, bool adj, bool varc) {
 
 void* pick(int R, bool adj, bool varc) { return pick_sp<false>(R, adj, varc); }
 
-size_t smem_bytes(int R, bool adj, bool varc) {
+size_t smem_bytes(int R, bool adj) {
   const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
-  const size_t nf = (adj && !varc) ? 2 : 1;
+  const size_t nf = adj ? 2 : 1;
   const size_t outbox = 2 * (size_t)(2 * R * (TX + TY)) * sizeof(unsigned long long);
   return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float) + outbox;
 }
 
-cudaError_t prepare(void* f, int R, bool adj, bool varc) {
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(R, adj, varc));
+cudaError_t prepare(void* f, int R, bool adj) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(R, adj));
 }
 
 }  // namespace
@@ -475,7 +456,7 @@ cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, 
 bool persist2d_supported(int R, bool) { return R == 1 || R == 3 || R == 5 || R == 7; }
 int persist2d_tile_x() { return TX; }
 int persist2d_tile_y() { return TY; }
-size_t persist2d_smem_bytes(int R, bool adj, bool varc) { return smem_bytes(R, adj, varc); }
+size_t persist2d_smem_bytes(int R, bool adj) { return smem_bytes(R, adj); }
 size_t persist2d_xbuf_words(int R, bool, int ntiles) { return (size_t)ntiles * 2 * 2 * R * (TX + TY); }
 
 int persist2d_max_ctas(int R, bool adj, bool varc) {
@@ -484,8 +465,8 @@ int persist2d_max_ctas(int R, bool adj, bool varc) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (prepare(f, R, adj, varc) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj, varc)) != cudaSuccess)
+  if (prepare(f, R, adj) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj)) != cudaSuccess)
     return 0;
   return sms * per_sm;
 }
@@ -496,22 +477,22 @@ cudaError_t persist2d_launch_layer(int R, bool adj, bool varc, const Persist2DAr
   int per_sm = 0, dev = 0, sms = 0;  // the layer variant must fit as many CTAs as the plan's tiles
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorUnknown;
-  cudaError_t e = prepare(f, R, adj, varc);
+  cudaError_t e = prepare(f, R, adj);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj, varc));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj));
   if (e != cudaSuccess) return e;
   if (per_sm * sms < nctas) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj, varc), st);
+  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj), st);
 }
 
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {
   void* f = pick(R, adj, varc);
   if (!f) return cudaErrorInvalidValue;
-  cudaError_t e = prepare(f, R, adj, varc);
+  cudaError_t e = prepare(f, R, adj);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj, varc), st);
+  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj), st);
 }
 
 }  // namespace pat

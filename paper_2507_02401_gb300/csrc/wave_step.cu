@@ -361,7 +361,7 @@ cudaError_t copy_launch(float* d, const float* s, long long n, cudaStream_t st) 
 namespace {
 template <int R>
 __global__ void grad_acc_kernel(double* __restrict__ gacc, const float* __restrict__ Q, const float* __restrict__ Qlo,
-                                const float* __restrict__ P, float coef, int nx, int ny, int nz, int dim,
+                                const float* __restrict__ P, float coef, int nx, int ny, int nz, int dim, int zform,
                                 const StepArgs a) {
   const long long N = (long long)nx * ny * nz;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
@@ -385,7 +385,9 @@ __global__ void grad_acc_kernel(double* __restrict__ gacc, const float* __restri
       }
       acc = fmaf(a.w[m], t, acc);
     }
-    const double q = (double)Q[i] + (Qlo ? (double)Qlo[i] : 0.0);
+    double q = (double)Q[i] + (Qlo ? (double)Qlo[i] : 0.0);
+    if (zform)  // the state holds Z = kappa Q
+      q /= a.kappa ? (double)a.kappa[i] + (double)a.kappa_lo[i] : (double)a.kappa0 + (double)a.kappa0_lo;
     gacc[i] += (double)coef * q * (double)acc;
   }
 }
@@ -402,14 +404,14 @@ __global__ void dfill_kernel(double* __restrict__ p, long long n) {
 }  // namespace
 
 cudaError_t grad_acc_launch(int R, double* gacc, const float* Q, const float* Qlo, const float* P, float coef,
-                            const StepArgs& a, int dim, cudaStream_t st) {
+                            const StepArgs& a, int dim, bool zform, cudaStream_t st) {
   const long long N = (long long)a.nx * a.ny * a.nz;
   const int blocks = grid_for(N);
   switch (R) {
-    case 1: grad_acc_kernel<1><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
-    case 3: grad_acc_kernel<3><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
-    case 5: grad_acc_kernel<5><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
-    case 7: grad_acc_kernel<7><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, a); break;
+    case 1: grad_acc_kernel<1><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, zform, a); break;
+    case 3: grad_acc_kernel<3><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, zform, a); break;
+    case 5: grad_acc_kernel<5><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, zform, a); break;
+    case 7: grad_acc_kernel<7><<<blocks, 256, 0, st>>>(gacc, Q, Qlo, P, coef, a.nx, a.ny, a.nz, dim, zform, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

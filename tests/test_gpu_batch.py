@@ -149,7 +149,8 @@ def test_batch_autograd_dot_product():
 def test_batch_64_uneven_instances_sampled():
     """64 instances, n in {128, ..., 512}, nt = ceil(sqrt(2) n / 0.3), order 8,
     64-512 sensors on circles or arcs: batched K against the oracle on the
-    smallest and the largest instance, 50-iteration batched solve against
+    smallest and the largest instance, batched K* of the noisy data on the
+    largest, 50-iteration batched solve against
     pat_solve on three instances and against the oracle's CG on the smallest."""
     torch = need_gpu()
     from paper_2507_02401_gb300 import Batch
@@ -165,6 +166,10 @@ def test_batch_64_uneven_instances_sampled():
         assert rel(ys[i].cpu().numpy(), wave.forward(w.x_true)) <= TOL_OP
     rng = np.random.default_rng(9)
     data = [synth.add_noise(y.cpu().numpy().astype(np.float64), w.noise, rng) for y, w in zip(ys, ws)]
+    # batched K* of the noisy data on the largest instance (512^2, 2414 steps)
+    w = ws[large]
+    wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
+    assert rel(batch.adjoint(data)[large].cpu().numpy(), wave.adjoint(data[large])) <= TOL_OP
     ss = [w.s[0] for w in ws]
     # alpha relative to lambda_max of E_s* K* K E_s (power iteration through the batch)
     g = torch.Generator(device="cuda").manual_seed(0)
