@@ -206,8 +206,10 @@ pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* 
  * time samples, sensors, wavelet, alpha and s may differ.  All instances'
  * 64-column tiles form one table; each time step of K or K* is one launch
  * over the tiles of the instances still running.  The tile height (64 or 32
- * rows) is chosen by timing both on the first steps of a batched K (an
- * autotuner; PAT_BATCH_TILE_Y=64|32 in the environment fixes it).
+ * rows) is chosen by timing both on the first steps of a batched K and K*
+ * (an autotuner; PAT_BATCH_TILE_Y=64|32 in the environment fixes it).  The
+ * batched K* keeps its state Z = kappa Q as a compensated pair in the plans'
+ * field buffers (it overwrites three of them).
  * Synchronises `stream`.  Errors: PAT_ERR_INVALID (NULL, duplicate or
  * ineligible plan), PAT_ERR_CUDA, PAT_ERR_OOM.
  */
@@ -238,7 +240,8 @@ pat_status pat_batch_solve(pat_batch* batch, const float* const* ys, const doubl
 /*
  * pat_batch_info — tile height in use, CTAs per step launch, nodes of the
  * captured CG-iteration graph (0 before the first solve) and the autotuner's
- * times (ms) of the 64-row and 32-row tiles.  Any output may be NULL.
+ * times (ms; the first steps of K plus K*) of the 64-row and 32-row tiles.
+ * Any output may be NULL.
  */
 pat_status pat_batch_info(pat_batch* batch, int* tile_rows, int* ctas, long long* graph_nodes, double* tune_ms);
 

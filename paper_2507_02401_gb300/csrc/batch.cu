@@ -180,24 +180,30 @@ pat_status batch_forward(pat_batch* b, cudaStream_t st, int steps = -1) {
 }
 
 // K* of every instance: the plans' sensor-data buffers -> the plans' image buffers.
-pat_status batch_adjoint(pat_batch* b, cudaStream_t st) {
+pat_status batch_adjoint(pat_batch* b, cudaStream_t st, int steps = -1) {
   for (pat_plan* p : b->plans) {
     PAT_TRY_CUDA(fill_launch(p->d_wv[0], p->N, 0.f, st));  // Z^{nt} = 0
     PAT_TRY_CUDA(fill_launch(p->d_wv[3], p->N, 0.f, st));  // Z_lo^{nt} = 0
     PAT_TRY_CUDA(fill_launch(p->d_wv[2], p->N, 0.f, st));  // G = 0
   }
-  for (int t = 0; t < b->max_nt; ++t)
+  const int T = steps < 0 ? b->max_nt : std::min(steps, b->max_nt);
+  for (int t = 0; t < T; ++t)
     PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, true), b->nctas_adj, st));
   return PAT_OK;
 }
 
-// Autotuner: times the first steps of a batched K with each tile shape and
-// keeps the faster (64 x 64 tiles, or 64 x 32 tiles with twice as many CTAs
-// in flight).  PAT_BATCH_TILE_Y=64|32 fixes the shape instead.
+// Autotuner: times the first steps of a batched K and of a batched K* with
+// each tile shape and keeps the faster pair (64 x 64 tiles, or 64 x 32 tiles
+// with twice as many CTAs in flight; the adjoint stages two boxes per tile, so
+// it fits fewer CTAs per SM than the forward).  PAT_BATCH_TILE_Y=64|32 fixes
+// the shape instead.
 pat_status tune(pat_batch* b, cudaStream_t st) {
   const char* env = getenv("PAT_BATCH_TILE_Y");
   if (env && (strcmp(env, "64") == 0 || strcmp(env, "32") == 0)) return build_tables(b, strcmp(env, "64") == 0 ? 0 : 1, st);
-  for (pat_plan* p : b->plans) PAT_TRY_CUDA(fill_launch(p->d_img, p->N, 0.f, st));
+  for (pat_plan* p : b->plans) {
+    PAT_TRY_CUDA(fill_launch(p->d_img, p->N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(p->d_ybuf, (long long)p->ns * p->nt, 0.f, st));
+  }
   const int steps = std::min(b->max_nt, 48);
   cudaEvent_t e0, e1;
   PAT_TRY_CUDA(cudaEventCreate(&e0));
@@ -209,6 +215,7 @@ pat_status tune(pat_batch* b, cudaStream_t st) {
     if (rc != PAT_OK) break;
     cudaEventRecord(e0, st);
     rc = batch_forward(b, st, steps);
+    if (rc == PAT_OK) rc = batch_adjoint(b, st, steps);
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       set_error("batched tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -32,10 +32,16 @@
 namespace pat {
 namespace {
 
-constexpr int TX = 64, RUN = 8, XH = 8, BW = TX + 2 * XH;
+constexpr int TX = 64, XH = 8, BW = TX + 2 * XH;
+
+// rows per thread: 8 for the forward; 4 for the adjoint, whose two stencils and two staged boxes
+// per tile need more registers and shared memory per cell (twice the threads per tile keep the
+// resident warps per SM up)
+constexpr int run_rows(bool adj) { return adj ? 4 : 8; }
 
 template <int R, int TY, bool ADJ>
 struct GB {
+  static constexpr int RUN = run_rows(ADJ);
   static constexpr int THREADS = (TX / 4) * (TY / RUN);
   static constexpr int PBOX = BW * (TY + 2 * R);  // floats (multiple of 32: 128-byte aligned stages)
   static constexpr int STAGE = (ADJ ? 2 : 1) * PBOX;
@@ -45,7 +51,7 @@ struct GB {
 template <int R, int TY, bool ADJ>
 __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(const BatchStepArgs a) {
   using G = GB<R, TY, ADJ>;
-  constexpr int THREADS = G::THREADS;
+  constexpr int THREADS = G::THREADS, RUN = G::RUN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
@@ -222,7 +228,7 @@ const void* kernel_for(int R, int variant, bool adj) {
   }
 }
 
-int threads_for(int variant) { return (TX / 4) * (batch_tile_y(variant) / RUN); }
+int threads_for(int variant, bool adj) { return (TX / 4) * (batch_tile_y(variant) / run_rows(adj)); }
 
 }  // namespace
 
@@ -243,7 +249,7 @@ int batch_max_ctas(int R, int variant, bool adj) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_for(variant), smem) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_for(variant, adj), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -257,7 +263,7 @@ cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nc
   if (!fn) return cudaErrorInvalidValue;
   const int grid = nctas < a.active ? nctas : a.active;
   void* args[] = {const_cast<BatchStepArgs*>(&a)};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant)), args, batch_smem(R, variant, adj), st);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant, adj)), args, batch_smem(R, variant, adj), st);
 }
 
 cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map) {

@@ -21,10 +21,14 @@
 // next tile's boxes (80 x (64+2R) floats, halo included, zero outside the
 // grid: P for the forward, Z and Z_lo for the adjoint) into the second of two
 // shared-memory stages while the CTA computes the current one.  Each thread
-// owns 4 columns x 8 consecutive rows: y neighbours come from a sliding
-// register window of 2R+1 rows, x neighbours from the shared-memory row; its
-// own D / G (and kappa) cells are loaded straight into registers (coalesced
-// 16-byte loads issued before the wait for the boxes).
+// owns 4 columns x 8 consecutive rows (4 rows in the adjoint, whose two boxes
+// and two stencils per cell need more registers: 256 threads of at most 170
+// registers per tile ran 6-19 % faster at 4096^2 than 128 threads of 238,
+// and faster than 256 threads capped at 128 registers, which spilled).
+// y neighbours come from a sliding register window of 2R+1 rows, x
+// neighbours from the shared-memory row; its own D / G (and kappa) cells are
+// loaded straight into registers (coalesced 16-byte loads issued before the
+// wait for the boxes).
 // Compulsory DRAM traffic per point-update: forward P and D read, P^{n+1} and
 // D^{n+1} written (16 B), plus kappa hi/lo (8 B) for a varying medium;
 // adjoint Z, Z_lo, G read and written (24 B), plus kappa (4 B) for a varying
@@ -42,8 +46,11 @@
 namespace pat {
 namespace {
 
-constexpr int TX = 64, TY = 64, RUN = 8;
-constexpr int TCOLS = TX / 4, TROWS = TY / RUN, THREADS = TCOLS * TROWS;  // 16 x 8 = 128
+constexpr int TX = 64, TY = 64, TCOLS = TX / 4;
+// rows per thread: 8 for the forward (128 threads per tile); 4 for the adjoint (256 threads), whose
+// two stencils and two staged boxes need more registers and shared memory per cell
+__host__ __device__ constexpr int run_rows(int mode) { return mode == 2 ? 4 : 8; }
+__host__ __device__ constexpr int threads_of(int mode) { return TCOLS * (TY / run_rows(mode)); }
 constexpr int XH = 8;            // box columns left of the tile (>= R, 16-byte aligned)
 constexpr int BW = TX + 2 * XH;  // box width, 80 floats
 
@@ -70,10 +77,11 @@ __device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid)
 //   adjoint  G' = G + inc,  Q' = a Q + b G', i.e. Z' = a Z + b kappa G'  (final step: x = G' + ((a-1)/b) Q)
 // Tiles that do not reach the layer use a = b = 1 without loading the factors.
 template <int R, int MODE, int SP>
-__global__ void __launch_bounds__(THREADS) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
+__global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mp,
                                                              const __grid_constant__ CUtensorMap ml, int* status,
                                                              long long timeout_ns) {
   constexpr bool VARC = MODE == 1, ADJ = MODE == 2;
+  constexpr int RUN = run_rows(MODE), THREADS = threads_of(MODE);
   using G = G2<R, ADJ ? 2 : 1>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage0 = reinterpret_cast<float*>(smem_raw);
@@ -305,7 +313,7 @@ int tma2d_ctas(int nx, int ny, int R, int mode, int sp) {
     const size_t smem = smem_for(R, mode);
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, THREADS, smem) != cudaSuccess || per < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_of(mode), smem) != cudaSuccess || per < 1) {
       cudaGetLastError();
       per = 1;
     }
@@ -316,7 +324,7 @@ int tma2d_ctas(int nx, int ny, int R, int mode, int sp) {
 }
 
 long long tma2d_threads(int nx, int ny, int R, int mode, int sp) {
-  return (long long)tma2d_ctas(nx, ny, R, mode, sp) * THREADS;
+  return (long long)tma2d_ctas(nx, ny, R, mode, sp) * threads_of(mode);
 }
 
 cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const CUtensorMap& p, const CUtensorMap& lo,
@@ -327,7 +335,7 @@ cudaError_t step2d_tma_launch(int R, int mode, int sp, const StepArgs& a, const 
   CUtensorMap map = p, mapl = lo;
   StepArgs args = a;
   void* params[] = {&args, &map, &mapl, &status, &timeout_ns};
-  return cudaLaunchKernel(fn, dim3(nctas), dim3(THREADS), params, smem_for(R, mode), st);
+  return cudaLaunchKernel(fn, dim3(nctas), dim3(threads_of(mode)), params, smem_for(R, mode), st);
 }
 
 }  // namespace pat
