@@ -80,8 +80,8 @@ WORKLOADS = {
                  "step and sampled at every second step (no inverse crime), 2% noise, db4 5 levels, s = 1, "
                  "alpha = 1e-2 (relative), 15 GMRES iterations on the paper's image-space system"),
         "kernel": "wave2d_persist_kernel<R=7> with the absorbing layer",
-        "profile": "step2d_tma_4096_o8.txt",
-        "sources": ("wave2d_tma.cu", "stencil.cuh", "tma.cuh"),
+        "profile": "wave2d_persist_512_o8_layer.txt",
+        "sources": ("wave2d_persist.cu", "stencil.cuh"),
         "oracle_nt": 40,
     },
 }
@@ -632,7 +632,8 @@ def run_limited(args):
                    "parallelism": f"replicas x{world} (independent instances per rank)"},
         "rel_error_by_s": errs, "J_per_iterate_s1": J_curve, "residual_per_iterate_s1": res_curve,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": spec["kernel"],
+                     "traffic": kernel_traffic("limited")[0] if plan.path == 1 else None, "peak_kind": peak_kind,
+                     "kernel": spec["kernel"],
                      "algorithmic_bytes_per_point_update": 12, "launch_ms": launch_ms, "launches_timed": launches,
                      "launch": "one K or K* application" if steps_per_launch > 1 else
                                "one time step (averaged over whole K / K* applications, injection included)",
