@@ -5,7 +5,7 @@ benchmark times (persistent engine for the 512 x 512 varying-medium case).
     sensors on a circle: K and K* against the oracle, then a 10-iteration
     solve (the full 100 iterations would cost the oracle ~200 wave solves).
   * 1024 x 1024, constant c, order 8, 3000 steps, 256 sensors on a 180-degree
-    arc: K and K*.
+    arc: K, and K* of noisy data simulated from the phantom and of random data.
   * 256^3, constant c, order 4, 4096 sensors on a sphere: K and K* over the
     first 60 steps (the per-step launch configuration is the one the 800-step
     run uses).
@@ -41,7 +41,10 @@ def test_arc_1024_operators():
     need_gpu()
     w = synth.workload("arc")
     plan, wave, _ = make_pair(w)
-    assert rel(plan.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= 1e-5
+    y_ref = wave.forward(w.x_true)
+    assert rel(plan.forward(w.x_true).cpu().numpy(), y_ref) <= 1e-5
+    y = synth.add_noise(y_ref, w.noise, np.random.default_rng(78))  # data simulated from the phantom
+    assert rel(plan.adjoint(y).cpu().numpy(), wave.adjoint(y)) <= 1e-5
     r = np.random.default_rng(2).standard_normal((w.ns, w.nt))
     assert rel(plan.adjoint(r).cpu().numpy(), wave.adjoint(r)) <= 1e-5
 
