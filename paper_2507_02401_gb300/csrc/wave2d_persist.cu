@@ -17,10 +17,13 @@
 // Precision.  kappa is applied as an unevaluated pair kappa_hi + kappa_lo:
 // with a constant medium a rounded kappa is the same everywhere and shifts
 // the phase of every mode coherently, step after step.  In the adjoint the
-// state Q integrates G over time and, in a closed (reflecting) box, grows an
-// order of magnitude beyond the result, so G and Q are kept as compensated
-// pairs (TwoSum) and the stencil receives kappa*Q as a hi + lo pair of FP32
-// fields (hi through the difference-form stencil, lo through the cheap form).
+// state Q integrates G over time and, in a closed (reflecting) box, grows far
+// beyond the result.  The adjoint therefore runs in Z = kappa Q,
+//   G^n = G^{n+1} + S^T r_n + L Z^{n+1},  Z^n = Z^{n+1} + kappa G^n,
+// with Z kept as a compensated pair Z + Z_lo (TwoSum) that is exchanged and
+// fed to the stencil as two FP32 fields (Z through the difference form, whose
+// rounding is relative to the differences, Z_lo through the cheap form); G is
+// plain.
 //
 // GB300 mapping.  The grid is cut into 64 x 32 tiles, one CTA per tile, all
 // co-resident (cooperative launch).  Each thread keeps its 2 x 4 cells' state
@@ -215,8 +218,8 @@ __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsign
 
 // SP: absorbing layer.  With per-cell factors a, b (1 outside the layer):
 //   forward  D' = a D + b inc (first step D' = (a-1) P + b inc), P' = P + D'
-//   adjoint  G' = G + inc, Q' = a Q + b G' (final x = ... + ((a-1)/b) Q); inside the layer the adjoint's
-//   compensation terms are carried approximately (the fields are being damped there).
+//   adjoint  G' = G + inc, Q' = a Q + b G', i.e. Z' = a Z + b kappa G' (final x = ... + ((a-1)/b) Q);
+//   inside the layer Z_lo is only damped (the fields are being damped there).
 template <int R, bool ADJ, bool VARC, bool SP>
 __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persist2DArgs a) {
   using G = Geo<R, ADJ>;
@@ -247,9 +250,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   if (region == 2 && tix > 0) nb = tile - 1;
   if (region == 3 && tix < a.tiles_x - 1) nb = tile + 1;
 
-  // forward: P, D ; adjoint: Q (in P), G (in D) and their compensation terms
+  // forward: P, D ; adjoint: Z (in P, with Z_lo in Pl), G (in D)
   float P[2][4], D[2][4], K[2][4];
-  float Pl[2][4], Dl[2][4], Kl[2][4];
+  float Pl[2][4], Kl[2][4];
   float SA[2][4], SB[2][4];  // layer factors (SP only)
   bool valid[2][4];
 #pragma unroll
@@ -267,7 +270,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       SB[rr][j] = (SP && v) ? a.sp_b[gi] : 1.f;
       D[rr][j] = 0.f;
       Pl[rr][j] = 0.f;
-      Dl[rr][j] = 0.f;
     }
   for (int i = t; i < 2 * G::NF * G::SBUF; i += NTHREADS) S0[i] = 0.f;
   if (ADJ)
@@ -327,15 +329,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
     if (ADJ) lap_2x4<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, a.w, L);
 
     if (k == nt - 1) {
-      if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L(kappa Q^1)
+      if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L Z^1
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if (!valid[rr][j]) continue;
             const int lr = r0 + rr, lc = c0 + j;
-            float xv = Jc[lr * TX + lc] + (D[rr][j] + Dl[rr][j]) + 0.5f * L[rr][j];
-            if (SP) xv = fmaf((SA[rr][j] - 1.f) / SB[rr][j], P[rr][j] + Pl[rr][j], xv);
+            float xv = Jc[lr * TX + lc] + D[rr][j] + 0.5f * L[rr][j];
+            if (SP && SA[rr][j] != 1.f)  // + ((a-1)/b) Q,  Q = (Z + Z_lo) / kappa
+              xv = fmaf((SA[rr][j] - 1.f) / SB[rr][j], (P[rr][j] + Pl[rr][j]) / (K[rr][j] + Kl[rr][j]), xv);
             a.out[(long long)(gy0 + lr) * nx + gx0 + lc] = xv;
           }
       }
@@ -368,26 +371,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
           const int li = (r0 + rr) * TX + c0 + j;
           const float inc = Jc[li] + L[rr][j];
           Jc[li] = 0.f;
-          float e;
-          float g = two_sum(D[rr][j], inc + Dl[rr][j], e);  // G += inc (compensated)
-          float gl = e;
-          float q, ql;
-          if (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) {  // Q = a Q + b G inside the layer
-            q = fmaf(SA[rr][j], P[rr][j], SB[rr][j] * g);
-            ql = fmaf(SA[rr][j], Pl[rr][j], SB[rr][j] * gl);
+          float g = D[rr][j] + inc;                            // G += S^T r + L Z
+          const float u = fmaf(K[rr][j], g, Kl[rr][j] * g);    // (kappa_hi + kappa_lo) G, rounded once
+          float z, zl;
+          if (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) {  // Z = a Z + b kappa G inside the layer
+            z = fmaf(SA[rr][j], P[rr][j], SB[rr][j] * u);
+            zl = SA[rr][j] * Pl[rr][j];
           } else {
-            q = two_sum(P[rr][j], g, e);  // Q += G (compensated)
-            ql = Pl[rr][j] + e;
+            float e;
+            z = two_sum(P[rr][j], u, e);  // Z += kappa G (compensated)
+            zl = Pl[rr][j] + e;
           }
-          if (!valid[rr][j]) g = gl = q = ql = 0.f;
+          if (!valid[rr][j]) g = z = zl = 0.f;
           D[rr][j] = g;
-          Dl[rr][j] = gl;
-          P[rr][j] = q;
-          Pl[rr][j] = ql;
-          // kappa (Q + Ql) as hi + lo: exact product error plus the small cross terms
-          const float wh = K[rr][j] * q;
-          V[rr][j] = wh;
-          Vl[rr][j] = fmaf(K[rr][j], q, -wh) + fmaf(K[rr][j], ql, Kl[rr][j] * q);
+          P[rr][j] = z;
+          Pl[rr][j] = zl;
+          V[rr][j] = z;
+          Vl[rr][j] = zl;
         }
     }
     float* Sn = S0 + ((k + 1) & 1) * G::NF * G::SBUF;
