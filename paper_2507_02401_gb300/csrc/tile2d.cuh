@@ -36,11 +36,19 @@ __device__ __forceinline__ float stencil_cell(const float4 (&win)[2 * R + 1], co
   return acc;
 }
 
-// Pair-form Laplacian of the 4 x RUN cells a thread owns in a box (pitch BW floats, R halo rows
-// above the tile, the thread's columns at XH + c0): lo[rr][j] for row r0 + rr.
+// Laplacian of the 4 x RUN cells a thread owns in a box (pitch BW floats, R halo rows above the tile,
+// the thread's columns at XH + c0): lo[rr][j] for row r0 + rr.  For the low part of a compensated
+// pair (a field of the order of the rounding error of its high part), so it takes the cheapest form,
+// sum_m w_m (a + b) - w_c c with the centre weight w_c = 4 sum_m w_m rounded once: 2 FP operations per
+// tap; the rounded w_c departs from a zero-sum stencil by a relative 2^-24 of a field that is itself
+// ~2^-24 of the state.
 template <int R, int RUN, int BW, int XH>
 __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r0, int c0,
                                             const float* __restrict__ w, float (&lo)[RUN][4]) {
+  float wc = 0.f;
+#pragma unroll
+  for (int m = 1; m <= R; ++m) wc += w[m];
+  wc *= 4.f;
   float4 win[2 * R + 1];
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(box + (r0 + i) * BW + XH + c0);
@@ -50,7 +58,14 @@ __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r
     float f[20];
     load_row20(box + (r0 + rr + R) * BW + c0 + XH - 8, f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) lo[rr][j] = stencil_cell<R, false>(win, f, j, w);
+    for (int j = 0; j < 4; ++j) {
+      float acc = -wc * f[8 + j];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], f4get(win[R + m], j) + f4get(win[R - m], j), acc);
+#pragma unroll
+      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], f[8 + j + m] + f[8 + j - m], acc);
+      lo[rr][j] = acc;
+    }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
   }
