@@ -89,8 +89,9 @@ struct Persist2DArgs {
 //      next = cur + d; with final = 1 (adjoint's last step) next = dbuf + c_lap L(kappa cur).
 //   3D (three-level form): next = c_cur cur - c_prev prev + c_lap kappa L cur
 //      (adjoint: L(kappa cur)).
-//   2D adjoint carries compensation terms: cur_lo/next_lo for Q, dbuf_lo for G,
-//      and feeds the stencil kappa*Q as a hi + lo pair.
+//   2D adjoint carries compensation terms in cur_lo/next_lo (and dbuf_lo): the TMA kernel keeps
+//      the state Z = kappa Q with its low part in cur_lo/next_lo (G plain); the plain kernel keeps
+//      Q with Q_lo there and G_lo in dbuf_lo, feeding the stencil kappa*Q as a hi + lo pair.
 struct StepArgs {
   int nx, ny, nz;
   float w[kMaxR + 1];
@@ -98,9 +99,9 @@ struct StepArgs {
   const float* kappa;     // or nullptr
   const float* kappa_lo;  // rounding residual of kappa, or nullptr
   const float* cur;    // P^n (forward) or Q^{n+1} (adjoint)
-  const float* cur_lo;  // 2D adjoint: compensation of Q^{n+1}
-  float* next_lo;       // 2D adjoint: compensation of Q^n
-  float* dbuf_lo;       // 2D adjoint: compensation of G
+  const float* cur_lo;  // 2D adjoint: compensation of Q^{n+1} (Z^{n+1} on the TMA kernel)
+  float* next_lo;       // 2D adjoint: compensation of Q^n (Z^n on the TMA kernel)
+  float* dbuf_lo;       // 2D adjoint, plain kernel: compensation of G
   const float* prev;   // 3D: P^{n-1} or Q^{n+2}   (nullptr = 0)
   float* dbuf;         // 2D: increment D (forward) / G (adjoint), updated in place
   int d_zero;          // 2D: treat the incoming increment as 0
@@ -115,9 +116,8 @@ struct StepArgs {
   const float* sens_w;
   int corners;
   float* y;
-  // 2D adjoint: injection S^T r_{inj_t} into dbuf before the step (nullptr = none).  The TMA kernel
-  // fuses it through per-tile lists (64 x 64 tiles, InjCell.local = ly * 64 + lx within the tile);
-  // otherwise a separate injection kernel runs first.
+  // Adjoint injection S^T r_{inj_t} (nullptr = none): 2D, into dbuf by a separate injection launch
+  // before the step; 3D, fused after the step through per-CTA lists (inj_tile_ptr / inj_tile).
   // 2D absorbing layer (nullptr = none): per-cell factors a, b of the damped update and the layer
   // width in cells (tiles farther than that from every face skip the factors)
   const float* sp_a;
