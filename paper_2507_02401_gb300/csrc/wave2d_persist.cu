@@ -28,9 +28,12 @@
 // GB300 mapping.  The grid is cut into 64 x 32 tiles, one CTA per tile, all
 // co-resident (cooperative launch).  Each thread keeps its 2 x 4 cells' state
 // in registers for the whole loop; the CTA keeps the current field plus an
-// R-deep halo in shared memory (double buffered).  After each step a CTA
-// writes its R-deep boundary strips to an L2-resident exchange buffer, every
-// value packed with the step it belongs to into one 64-bit word; an aligned
+// R-deep halo in shared memory (double buffered).  After each step the
+// threads that own boundary cells write the R-deep strips straight to an
+// L2-resident exchange buffer (relaxed GPU-scope stores; 93.4 against 92.3
+// reconstruction iterations/s at 512^2 when they were staged in shared memory
+// and handed to the TMA engine), every value packed with the step it belongs
+// to into one 64-bit word; an aligned
 // 64-bit access is single-copy atomic, so a neighbour that reads a word with
 // the expected tag has the right value: no flags, no fences, one L2 round
 // trip per exchange and one CTA barrier per step.  Every wait is bounded by a
@@ -86,18 +89,15 @@ __device__ __forceinline__ bool tag_ok(u64 w, unsigned step) {
 __device__ __forceinline__ float word_hi(u64 w) { return __uint_as_float((unsigned)(w & 0xffffffffull)); }
 __device__ __forceinline__ float word_lo(u64 w) { return __uint_as_float((unsigned)(w >> 32) & ~0xffu); }
 
-// TMA bulk copy of a shared-memory segment to global memory (async proxy).
-__device__ __forceinline__ void bulk_store(u64* gdst, const u64* ssrc, unsigned bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(ssrc);
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(sa), "r"(bytes)
-               : "memory");
+// Exchange words are written with relaxed GPU-scope stores straight from the
+// owning threads (aligned 64-bit elements: single-copy atomic) and read with
+// relaxed GPU-scope loads.
+__device__ __forceinline__ void st_word2(u64* p, u64 a, u64 b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// wait until at most one committed group is still reading its shared-memory source
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
+__device__ __forceinline__ void st_word(u64* p, u64 a) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
 __device__ __forceinline__ void ld_word2(const u64* p, u64& a, u64& b) {
   asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
@@ -108,11 +108,11 @@ __device__ __forceinline__ u64 ld_word(const u64* p) {
 }
 
 // Write the thread's 2x4 block of the new state into the shared field
-// buffer(s) Sn (second field at Sn + SBUF) and, packed and tagged, into the
-// shared outbox O laid out like the boundary strips:
-// [top R x TX][bottom R x TX][left TY x R][right TY x R].
+// buffer(s) Sn (second field at Sn + SBUF) and, packed and tagged, its
+// boundary cells into the tile's exchange slot X in global memory, laid out
+// as the boundary strips [top R x TX][bottom R x TX][left TY x R][right TY x R].
 template <int R, bool ADJ>
-__device__ __forceinline__ void store_state(float* Sn, u64* O, const float V[2][4], const float Vl[2][4], int r0,
+__device__ __forceinline__ void store_state(float* Sn, u64* X, const float V[2][4], const float Vl[2][4], int r0,
                                             int c0, unsigned step) {
   constexpr int SBUF = Geo<R, ADJ>::SBUF;
 #pragma unroll
@@ -127,42 +127,19 @@ __device__ __forceinline__ void store_state(float* Sn, u64* O, const float V[2][
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] = pack<ADJ>(V[rr][j], Vl[rr][j], step);
     u64* dst = nullptr;
-    if (row < R) dst = O + row * TX + c0;
-    if (row >= TY - R) dst = O + R * TX + (row - (TY - R)) * TX + c0;
+    if (row < R) dst = X + row * TX + c0;
+    if (row >= TY - R) dst = X + R * TX + (row - (TY - R)) * TX + c0;
     if (dst) {  // TY >= 2R: a row is in at most one of the two strips
-      *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(w[0], w[1]);
-      *reinterpret_cast<ulonglong2*>(dst + 2) = make_ulonglong2(w[2], w[3]);
+      st_word2(dst, w[0], w[1]);
+      st_word2(dst + 2, w[2], w[3]);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = c0 + j;
-      if (col < R) O[2 * R * TX + row * R + col] = w[j];
-      if (col >= TX - R) O[2 * R * TX + TY * R + row * R + (col - (TX - R))] = w[j];
+      if (col < R) st_word(X + 2 * R * TX + row * R + col, w[j]);
+      if (col >= TX - R) st_word(X + 2 * R * TX + TY * R + row * R + (col - (TX - R)), w[j]);
     }
   }
-}
-
-// Hand the warp's rows [4w, 4w+4) of the outbox to the TMA engine: up to four
-// contiguous segments (top, bottom, left, right strips).
-// All lanes must have written their words; lane 0 issues and commits.
-template <int R>
-__device__ __forceinline__ void publish_warp(u64* X, const u64* O, int warp, int lane) {
-  fence_proxy_async_smem();
-  __syncwarp();
-  if (lane != 0) return;
-  const int w4 = 4 * warp;
-  {
-    const int fo = 0;
-    const int tlo = w4, thi = min(w4 + 4, R);
-    if (tlo < thi) bulk_store(X + fo + tlo * TX, O + fo + tlo * TX, (unsigned)((thi - tlo) * TX * 8));
-    const int blo = max(w4, TY - R), bhi = w4 + 4;
-    if (blo < bhi)
-      bulk_store(X + fo + R * TX + (blo - (TY - R)) * TX, O + fo + R * TX + (blo - (TY - R)) * TX,
-                 (unsigned)((bhi - blo) * TX * 8));
-    bulk_store(X + fo + 2 * R * TX + w4 * R, O + fo + 2 * R * TX + w4 * R, (unsigned)(4 * R * 8));
-    bulk_store(X + fo + 2 * R * TX + TY * R + w4 * R, O + fo + 2 * R * TX + TY * R + w4 * R, (unsigned)(4 * R * 8));
-  }
-  bulk_commit();
 }
 
 // Copy the halo of state `step` from the neighbour's strips X into the shared
@@ -226,7 +203,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   extern __shared__ float4 smem4[];
   float* S0 = reinterpret_cast<float*>(smem4);  // [slot][field] buffers
   float* J0 = S0 + 2 * G::NF * G::SBUF;         // adjoint injection accumulators, 2 x TY x TX
-  u64* OB = reinterpret_cast<u64*>(J0 + (ADJ ? 2 * TX * TY : 0));  // outbox, 2 parities x SLOT words
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -278,8 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   __syncthreads();
 
   {  // publish state 0 (forward: x; adjoint: zero)
-    store_state<R, ADJ>(S0, OB, P, Pl, r0, c0, 0u);
-    publish_warp<R>(xbuf + (size_t)tile * 2 * G::SLOT, OB, warp, lane);
+    store_state<R, ADJ>(S0, xbuf + (size_t)tile * 2 * G::SLOT, P, Pl, r0, c0, 0u);
   }
 
   for (int k = 0; k < nt; ++k) {
@@ -391,13 +366,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
         }
     }
     float* Sn = S0 + ((k + 1) & 1) * G::NF * G::SBUF;
-    u64* On = OB + ((k + 1) & 1) * G::SLOT;
-    if (lane == 0) bulk_wait_read_1();  // the copy that last read this outbox half is done
-    __syncwarp();
-    store_state<R, ADJ>(Sn, On, V, Vl, r0, c0, (unsigned)(k + 1));
-    publish_warp<R>(xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT, On, warp, lane);
+    store_state<R, ADJ>(Sn, xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT, V, Vl, r0, c0, (unsigned)(k + 1));
   }
-  if (lane == 0) bulk_wait_all();
 
 }
 
@@ -435,8 +405,7 @@ void* pick(int R, bool adj, bool varc) { return pick_sp<false>(R, adj, varc); }
 size_t smem_bytes(int R, bool adj) {
   const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
   const size_t nf = adj ? 2 : 1;
-  const size_t outbox = 2 * (size_t)(2 * R * (TX + TY)) * sizeof(unsigned long long);
-  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float) + outbox;
+  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float);
 }
 
 cudaError_t prepare(void* f, int R, bool adj) {
