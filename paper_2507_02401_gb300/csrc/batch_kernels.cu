@@ -8,7 +8,7 @@
 //
 // The adjoint state Z integrates G over time and, in a closed box, grows far
 // beyond the result: it is kept as a compensated pair Z + Z_lo (TwoSum), the
-// stencil sees Z through the difference form and Z_lo through the pair form,
+// stencil sees Z through the difference form and Z_lo through the sum form,
 // as in the single-instance 2D step kernel.
 //
 // The tiles (64 columns x 64 or 32 rows) of all instances form one table,

@@ -10,7 +10,7 @@
 // box Z integrates G over time and grows far beyond the result, so Z is kept
 // as a compensated pair Z + Z_lo (TwoSum), the stencil sees both parts
 // (Z through the difference form (a - c) + (b - c), whose rounding is relative
-// to the differences, Z_lo through the cheap pair form), and G is plain.
+// to the differences, Z_lo through the cheapest sum form), and G is plain.
 // FP32 emulation of the 512^2, 1500-step, order-8 adjoint with noisy data
 // simulated from a phantom: 1.9e-5 for the plain pair-form recurrence
 // (constant and varying medium), 1.5e-5 with the difference form alone,
