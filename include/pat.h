@@ -117,6 +117,9 @@ pat_status pat_forward(pat_plan* plan, const float* x, float* y, void* stream);
  * pat_adjoint — x = K* y, the exact transpose of pat_forward (reverse-time
  * recurrence with transposed sensor injection).  Paper Sec. 4 (K* needed by
  * the matrix-free solver).   y  ns*nt floats.   x  N floats.
+ * FP32 fields; in 2D the adjoint state (kappa Q, which integrates the data
+ * over time) is carried as a compensated pair, so the result stays within
+ * ~1e-6 relative of the exact transpose for data simulated from a phantom.
  */
 pat_status pat_adjoint(pat_plan* plan, const float* y, float* x, void* stream);
 
