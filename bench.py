@@ -1,21 +1,23 @@
 #!/usr/bin/env python
 """Throughput of the wavelet-Sobolev PAT reconstruction on GB300.
 
-One step = one full reconstruction of the 2D 512 x 512 workload: smooth
-random speed of sound in [1400, 1600] m/s, order-8 staggered stencil, 1500
-time samples, 512 sensors on a circle, db4 with 5 levels, and 100 CG
-iterations on (E_s* K* K E_s + alpha I) u = E_s* K* y (plus the right-hand
-side's K* and the final E_s u).  Steps cycle through s in {1, 2} x alpha in
-{1e-3, 1e-2} (alpha relative to lambda_max of E_s* K* K E_s, estimated by
-power iteration before timing).  Metric: reconstruction iterations per second
-(one K + one K* per iteration), whole job.
+One step = one full reconstruction of the 3D 256^3 workload (the largest
+single-GPU configuration): constant speed of sound 1500 m/s, order-4
+staggered stencil, 800 time samples, 4096 sensors on a Fibonacci sphere,
+p0 = a vessel tree plus 5 blobs, 1% noise, separable 3D db4 with 4 levels,
+s = 1, alpha = 1e-2 relative to lambda_max of E_s* K* K E_s (estimated by
+power iteration before timing), and 30 CG iterations on
+(E_s* K* K E_s + alpha I) u = E_s* K* y (plus the right-hand side's K* and
+the final E_s u).  Metric: reconstruction iterations per second (one K + one
+K* per iteration), whole job.
 
 With N > 1 (torchrun) every rank solves its own independently seeded
 instance (weak scaling, no data-path collective).
 
---workload tree3d times the 3D 256^3 order-4 workload instead (4096
-sensors on a sphere, 800 time samples, 3D db4 with 4 levels, 30 CG
-iterations per step).
+--workload vessels times the 2D 512 x 512 workload instead: smooth random
+speed of sound in [1400, 1600] m/s, order-8 stencil, 1500 time samples, 512
+sensors on a circle, db4 with 5 levels, 100 CG iterations per step, steps
+cycling through s in {1, 2} x alpha in {1e-3, 1e-2}.
 
 --workload batch64 times 64 independent reconstructions of uneven size
 (n in {128..512}, order 8, 50 CG iterations each) through the batched
@@ -53,7 +55,7 @@ if ROOT not in sys.path:
 
 METRIC = "reconstruction iterations/sec (K+K* pairs)"
 UNIT = "iterations/s"
-WORKLOAD = "vessels"
+WORKLOAD = "tree3d"
 # per workload: description, timed kernel, committed ncu summary and the sources it was taken on
 WORKLOADS = {
     "vessels": {
@@ -788,6 +790,8 @@ def run_batch(args):
         "gpu_launches": int(args.steps * (iters * info["graph_nodes"] + max_nt + 12 * n_inst + 1)),
         "clocks": clocks,
     }
+    if rank == 0 and args.accuracy:
+        line["accuracy_vs_oracle"] = batch_accuracy(ws, plans, batch, iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -795,6 +799,89 @@ def run_batch(args):
         dist.destroy_process_group()
     batch.close()
     return 0
+
+
+def oracle_lambda_max(wave, wav, s, iters=15, seed=0):
+    """Power iteration on E_s* K* K E_s with the FP64 oracle."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(wave.N)
+    v /= np.linalg.norm(v)
+    H = oracle.normal_op(wave, wav, s, 0.0)
+    lam = 0.0
+    for _ in range(iters):
+        hv = H(v)
+        lam = float(np.linalg.norm(hv))
+        v = hv / lam
+    return lam
+
+
+def batch_accuracy(ws, plans, batch, iters, n_max=192, n_conv=128):
+    """Accuracy of the batched and of the sequential (pat_solve) path against
+    the FP64 oracle, on every instance of the batched workload with n <= n_max:
+    data simulated by the oracle, alpha = alpha_rel * the oracle's lambda_max
+    (the same absolute alpha on every side), the oracle's CG at the same
+    iteration count and, for n <= n_conv, the oracle's converged minimiser
+    (CG to ||b - H u|| <= 1e-10 ||b||).  Instances above n_max keep their
+    GPU-simulated data (they run in the batch but are not compared)."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2507_02401_gb300 import _lib
+    idx = [i for i, w in enumerate(ws) if w.shape[0] <= n_max]
+    ys, alphas = {}, {}
+    ref = {}
+    t0 = time.perf_counter()
+    for i in idx:
+        w = ws[i]
+        wave = oracle.Wave(w.shape, w.h, w.dt, w.nt, w.order, w.c_array(), w.sensors)
+        wav = oracle.Wavelet(w.shape, w.family, w.levels)
+        y = synth.add_noise(wave.forward(w.x_true), w.noise, np.random.default_rng(3000 + i))
+        a = w.alpha[0] * oracle_lambda_max(wave, wav, w.s[0])
+        _, x_o, _ = oracle.cg(wave, wav, y, a, w.s[0], iters)
+        conv = None
+        if w.shape[0] <= n_conv:
+            _, x_c, k, rr = oracle.cg_converged(wave, wav, y, a, w.s[0])
+            conv = (x_c, k, rr)
+        ys[i], alphas[i], ref[i] = y, a, (x_o, conv)
+    t_oracle = time.perf_counter() - t0
+    # GPU: one batched solve of all instances, then pat_solve per compared instance
+    yb = [torch.as_tensor(ys[i] if i in ys else np.zeros((p.ns, p.nt)), dtype=torch.float32, device="cuda")
+          for i, p in enumerate(plans)]
+    ab = [alphas.get(i, ws[i].alpha[0]) for i in range(len(ws))]
+    ss = [w.s[0] for w in ws]
+    xs = [torch.empty(w.shape, device="cuda") for w in ws]
+    rc, per = _lib.pat_batch_solve(batch.handle, yb, ab, ss, iters, xs, torch.cuda.current_stream())
+    assert rc == 0, (rc, per)
+    rows = []
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+    for i in idx:
+        w = ws[i]
+        _, xq, _ = plans[i].solve(yb[i], ab[i], ss[i], iters)
+        xb_np, xq_np = xs[i].cpu().numpy().astype(np.float64), xq.cpu().numpy().astype(np.float64)
+        x_o, conv = ref[i]
+        row = {"i": i, "n": w.shape[0], "s": w.s[0], "alpha_rel": w.alpha[0],
+               "batched_vs_oracle": rel(xb_np, x_o), "sequential_vs_oracle": rel(xq_np, x_o)}
+        if conv is not None:
+            x_c, k, rr = conv
+            row.update({"oracle_vs_converged": rel(x_o, x_c), "batched_vs_converged": rel(xb_np, x_c),
+                        "sequential_vs_converged": rel(xq_np, x_c), "converged_iters": k,
+                        "converged_rel_residual": rr})
+        rows.append(row)
+    bands = {}
+    for name, lo, hi in (("alpha_rel<1e-3", 0.0, 1e-3), ("1e-3<=alpha_rel<1e-2", 1e-3, 1e-2),
+                         ("alpha_rel>=1e-2", 1e-2, 1.0)):
+        sel = [r for r in rows if lo <= r["alpha_rel"] < hi]
+        if sel:
+            bands[name] = {"instances": len(sel),
+                           "max_batched_vs_oracle": max(r["batched_vs_oracle"] for r in sel),
+                           "max_sequential_vs_oracle": max(r["sequential_vs_oracle"] for r in sel)}
+    return {"compared": len(rows), "iters": iters, "oracle_seconds": t_oracle, "by_conditioning": bands,
+            "instances": rows}
 
 
 def run_prior_sweep(args):
@@ -832,6 +919,63 @@ def run_prior_sweep(args):
     return 0
 
 
+def dwt_bytes_per_cell(dim, levels):
+    """Algorithmic bytes of one E_s or E_s* per grid cell: every level reads
+    its input and writes its output once (8 B per cell of the level), the
+    level sizes falling by 2^dim: 8 (1 - 2^(-dim m)) / (1 - 2^-dim)."""
+    r = 2.0 ** -dim
+    return 8.0 * (1.0 - r ** levels) / (1.0 - r)
+
+
+def run_dwt_sweep(args):
+    """The wavelet kernels (E_s = W^T S_s synthesis and E_s* = S_s W analysis,
+    periodic db4) on HBM-sized grids: each application timed alone with CUDA
+    events on the launching stream, a 256 MiB L2 flush before each, against
+    the algorithmic bytes of dwt_bytes_per_cell."""
+    import torch
+    from paper_2507_02401_gb300 import Plan
+    peak, peak_kind = peaks()
+    cases = [((2048, 2048), 5), ((4096, 4096), 5), ((8192, 8192), 5), ((256, 256, 256), 4), ((512, 512, 512), 4)]
+    if args.only:
+        cases = [c for c in cases if "x".join(map(str, c[0])) == args.only]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    for shape, levels in cases:
+        h = 1e-4
+        sens = np.zeros((0, len(shape)))
+        plan = Plan(shape, h, 0.3 * h / 1500.0, 2, 2, 1500.0, sens, 4, levels)
+        N = int(np.prod(shape))
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn(shape, device="cuda", generator=g)
+        u = torch.empty(N, device="cuda")
+        bpc = dwt_bytes_per_cell(len(shape), levels)
+        line = {"dwt_sweep": "x".join(map(str, shape)), "wavelet": f"db4, {levels} levels, periodic",
+                "algorithmic_bytes_per_cell": round(bpc, 3), "peak_gbs": peak, "peak_kind": peak_kind,
+                "l2": "256 MiB buffer written before every timed application"}
+        reps = max(args.steps, 10)
+        for name, fn in (("EsT", lambda: plan.EsT(x, 1.0, out=u)), ("Es", lambda: plan.Es(u, 1.0, out=x))):
+            for _ in range(args.warmup):
+                fn()
+            ms = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            us = ms * 1e3 / reps
+            gbs = N * bpc / us / 1e3
+            line[name] = {"us_per_application": round(us, 2), "algorithmic_gbs": round(gbs, 1),
+                          "frac": round(gbs / peak, 3)}
+        print(json.dumps(line), flush=True)
+        plan.close()
+        del x, u
+        torch.cuda.empty_cache()
+    return 0
+
+
 def plan_varc(w):
     return np.ndim(w.c) != 0 and float(np.max(w.c)) != float(np.min(w.c))
 
@@ -846,10 +990,15 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="override CG iterations per step")
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle CG iterations in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="with --workload batch64: per-instance errors against the FP64 oracle (n <= 192) and its "
+                         "converged minimiser (n = 128), outside the timed region")
     ap.add_argument("--power-iters", type=int, default=20, help="power iterations for lambda_max")
     ap.add_argument("--only", default="", help="with --sweep: run only a grid (256x256x256) or a case (4096x4096-o8)")
     ap.add_argument("--prior-sweep", action="store_true",
                     help="time E_s of the wavelet and Fourier prior forms on 2D grids instead")
+    ap.add_argument("--dwt-sweep", action="store_true",
+                    help="time the wavelet kernels (E_s, E_s*) on 2D 2048^2..8192^2 and 3D 256^3, 512^3 instead")
     ap.add_argument("--sweep", action="store_true",
                     help="time the per-step wave engines on 2D 2048^2..16384^2 (orders 2, 8) and 3D grids instead")
     args = ap.parse_args()
@@ -860,6 +1009,8 @@ def main():
         return run_sweep(args)
     if args.prior_sweep:
         return run_prior_sweep(args)
+    if args.dwt_sweep:
+        return run_dwt_sweep(args)
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "limited":

@@ -183,6 +183,23 @@ pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, dou
                                float* u, float* x, double* J, void* stream);
 
 /*
+ * pat_objective — the Tikhonov functional whose minimiser pat_solve computes
+ * (paper Sec. 3, the variational problem behind Eq. (linear_minimization),
+ * in wavelet coefficients):
+ *     J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2
+ * and, optionally, its gradient E_s* K* (K E_s u - y) + alpha u.  Reductions
+ * in FP64 in a fixed order (bit-reproducible).  Synchronous.
+ *   y      Ns*nt floats, u  N coefficients (device or host arrays).
+ *   alpha  >= 0 (absolute), s  finite.
+ *   J      HOST pointer to one double (output).
+ *   grad   NULL or N floats (device or host; output).
+ * Uses the plan's image and data buffers (not concurrently with other calls on
+ * the same plan).  PAT_ERR_INVALID for NULL y / u / J or a non-finite alpha or s.
+ */
+pat_status pat_objective(pat_plan* plan, const float* y, double alpha, double s, const float* u, double* J,
+                         float* grad, void* stream);
+
+/*
  * pat_solve_batched — B independent pat_solve problems (each with its own
  * plan, data, alpha and s; a common iteration count) advanced together.
  * When every plan qualifies for a batch (see pat_batch_create) and ys / xs
@@ -247,6 +264,23 @@ pat_status pat_batch_solve(pat_batch* batch, const float* const* ys, const doubl
  * Any output may be NULL.
  */
 pat_status pat_batch_info(pat_batch* batch, int* tile_rows, int* ctas, long long* graph_nodes, double* tune_ms);
+
+/*
+ * pat_batch_launch — launch form of the batched K and K*.  Form 1: one
+ * launch per time step (each walks the tiles still running).  Form 2: one
+ * cooperative launch per application: every CTA co-resident, a grid-wide
+ * barrier between time steps (each wait bounded: a CTA that gives up records
+ * PAT_ERR_TIMEOUT, which the others see at their next barrier, and all
+ * leave).  At creation the autotuner times both on the first steps of a K
+ * plus K* and keeps the faster.
+ *   mode    -1: query only; 0: the autotuner's choice; 1: per step; 2: one
+ *           launch per application.  Changing the form drops the captured
+ *           CG-iteration graph (re-captured at the next solve).
+ *   runall  NULL or out: 1 when form 2 is in use.
+ *   ms      NULL or out, 2 doubles: the autotuner's times (ms) of forms 1, 2.
+ * Not in the paper (its one reconstruction has no batch).
+ */
+pat_status pat_batch_launch(pat_batch* batch, int mode, int* runall, double* ms);
 
 /*
  * pat_grad_kappa — g = d<r, K x>/d kappa per cell, kappa = (c dt / h)^2: the
@@ -348,8 +382,13 @@ pat_status pat_plan_profile_read(pat_plan* plan, long long* kernels, int* wave_c
  *                 both divisible by 2^levels.  Larger grids are rejected with
  *                 PAT_ERR_INVALID and a message naming the limit.
  *   family, levels, level_offset, s   as for pat_plan_create / pat_EsT.
- *   x             device array of nx*ny floats (row-major, x fastest).
- *   u             device array of nx*ny floats, coefficient layout of pat_EsT.
+ *   x             device array of nx*ny floats (row-major, x fastest) on the
+ *                 current device.
+ *   u             device array of nx*ny floats, coefficient layout of pat_EsT,
+ *                 on the current device; x and u must not overlap (rejected
+ *                 with PAT_ERR_INVALID).  The library cannot see the arrays'
+ *                 lengths: arrays shorter than nx*ny floats are the caller's
+ *                 error and corrupt memory.
  *   stream        cudaStream_t (asynchronous, like pat_EsT).
  * The transform's scratch (2 MiB) is a fixed array in device memory that
  * every device loading the library holds until the process exits.  The first
@@ -358,7 +397,8 @@ pat_status pat_plan_profile_read(pat_plan* plan, long long* kernels, int* wave_c
  * All calls share the one array: calls that overlap on the GPU (two streams,
  * two host threads) race and corrupt each other's results, so serialise them.
  * Nothing in the array needs to start at zero: every call writes each scratch
- * element before reading it.
+ * element before reading it.  The cached address is not refreshed after
+ * cudaDeviceReset: calls after a reset of the device are not supported.
  */
 pat_status pat_EsT_noalloc(int nx, int ny, int family, int levels, int level_offset, double s, const float* x,
                            float* u, void* stream);

@@ -15,4 +15,4 @@ seeded input generators of `synth`.
 from .fdtd import Wave, set_threads, max_threads, sponge_sigma, sponge_sigma_max  # noqa: F401
 from .wavelet import Wavelet, daubechies, highpass  # noqa: F401
 from .fourier import FourierPrior  # noqa: F401
-from .solve import cg, normal_op, rhs, Breakdown  # noqa: F401
+from .solve import cg, cg_converged, normal_op, rhs, Breakdown  # noqa: F401

@@ -58,3 +58,32 @@ def cg(wave, wav, y, alpha, s, iters, u0=None):
         p = r + (rr_new / rr) * p
         rr = rr_new
     return u, wav.Es(u, s), np.array(log)
+
+
+def cg_converged(wave, wav, y, alpha, s, rtol=1e-10, max_iters=3000):
+    """The minimiser itself (reading A14's "converged solution"): the same CG,
+    run until ||b - H u|| <= rtol ||b|| with the residual recomputed from u
+    (not the recurrence) at the end.  Returns (u, x, iterations, rel_res)."""
+    H = normal_op(wave, wav, s, alpha)
+    b = rhs(wave, wav, y, s)
+    nb = float(np.linalg.norm(b))
+    u = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    k = 0
+    while k < max_iters and np.sqrt(rr) > rtol * nb:
+        q = H(p)
+        pq = float(p @ q)
+        if not np.isfinite(pq) or pq <= 0.0:
+            raise Breakdown(f"p.q = {pq}")
+        a = rr / pq
+        u += a * p
+        r -= a * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        k += 1
+    rel_res = float(np.linalg.norm(b - H(u)) / nb)
+    return u, wav.Es(u, s), k, rel_res
+

@@ -46,6 +46,8 @@ SIGNATURES = [
                                 c_void_p]),
     ("pat_solve_landweber", c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    ("pat_objective", c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, ctypes.POINTER(c_double),
+                              c_void_p, c_void_p]),
     ("pat_solve_batched", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p]),
     ("pat_batch_create", c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
@@ -55,6 +57,7 @@ SIGNATURES = [
     ("pat_batch_solve", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("pat_batch_info", c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_longlong),
                                ctypes.POINTER(c_double)]),
+    ("pat_batch_launch", c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     ("pat_grad_kappa", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("pat_plan_check", c_int, [c_void_p, c_void_p]),
     ("pat_plan_set_path", c_int, [c_void_p, c_int]),
@@ -279,9 +282,36 @@ def pat_plan_profile_read(plan):
 
 
 def pat_EsT_noalloc(nx, ny, family, levels, level_offset, s, x, u, stream=None):
-    """E_s* of a 2D image without any device allocation (device arrays only)."""
+    """E_s* of a 2D image without any device allocation (device arrays only).
+
+    The C side cannot see array lengths, so tensors are checked here: float32,
+    on a CUDA device, at least nx*ny elements."""
+    for name, t in (("x", x), ("u", u)):
+        if hasattr(t, "data_ptr"):
+            import torch
+            if t.dtype != torch.float32 or not t.is_cuda or t.numel() < int(nx) * int(ny):
+                raise ValueError(f"pat_EsT_noalloc: {name} must be a float32 CUDA tensor of at least nx*ny = "
+                                 f"{int(nx) * int(ny)} elements (got {t.dtype}, {t.device}, {t.numel()})")
     return _check(load().pat_EsT_noalloc(int(nx), int(ny), int(family), int(levels), int(level_offset), float(s),
                                          ptr(x), ptr(u), stream_handle(stream)))
+
+
+def pat_objective(plan, y, alpha, s, u, grad=None, stream=None):
+    """J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 (returned); the gradient
+    is written to `grad` when given."""
+    J = c_double()
+    _check(load().pat_objective(plan, ptr(y), float(alpha), float(s), ptr(u), ctypes.byref(J), ptr(grad),
+                                stream_handle(stream)))
+    return J.value
+
+
+def pat_batch_launch(batch, mode=-1):
+    """Set (mode 0 auto, 1 per step, 2 one launch per application) or query the
+    batched launch form; returns (runall, [ms per-step, ms one-launch])."""
+    ra = c_int()
+    ms = (c_double * 2)()
+    _check(load().pat_batch_launch(batch, int(mode), ctypes.byref(ra), ms))
+    return ra.value, [ms[0], ms[1]]
 
 
 def pat_last_error():

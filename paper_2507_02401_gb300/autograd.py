@@ -132,7 +132,27 @@ def EsT(plan, s, x):
     return PatEsT.apply(plan, s, x)
 
 
+class PatObjective(torch.autograd.Function):
+    """J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 and its gradient
+    E_s* K* (K E_s u - y) + alpha u, both computed by the library in one call
+    (pat_objective); backward scales the stored gradient."""
+
+    @staticmethod
+    def forward(ctx, plan, u, y, alpha, s):
+        grad = torch.empty(plan.N, device=u.device, dtype=torch.float32)
+        J = _lib.pat_objective(plan.handle, _f32(y), alpha, s, _f32(u).reshape(-1), grad, _stream())
+        ctx.save_for_backward(grad)
+        ctx.u_shape = u.shape
+        return torch.tensor(J, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (grad,) = ctx.saved_tensors
+        gu = (grad * gJ.to(torch.float32)).reshape(ctx.u_shape)
+        return None, gu, None, None, None
+
+
 def reconstruction_loss(plan, u, y, alpha, s):
-    """J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 (accumulated in float64)."""
-    r = K(plan, Es(plan, s, u)) - y
-    return 0.5 * (r.double() ** 2).sum() + 0.5 * alpha * (u.double() ** 2).sum()
+    """J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 (float64 scalar, from the
+    library); differentiable in u."""
+    return PatObjective.apply(plan, u, y, alpha, s)

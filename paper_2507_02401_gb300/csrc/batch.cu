@@ -33,6 +33,8 @@ void bfree_all(pat_batch* b) {
   b->d_tiles = nullptr;
   b->d_maps = nullptr;
   b->d_status = nullptr;
+  b->d_active = nullptr;
+  b->d_bar = nullptr;
 }
 
 bool device_ptr(const void* p) {
@@ -144,6 +146,9 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
   PAT_TRY(balloc(b, &b->d_maps, maps.size(), "batch tensor maps"));  // cudaMalloc: 256-byte aligned
   PAT_TRY(balloc(b, &b->d_status, 1, "batch status"));
   PAT_TRY_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
+  PAT_TRY(balloc(b, &b->d_active, (size_t)b->max_nt, "batch active tiles per step"));
+  PAT_TRY_CUDA(cudaMemcpyAsync(b->d_active, b->active.data(), sizeof(int) * b->max_nt, cudaMemcpyHostToDevice, st));
+  PAT_TRY(balloc(b, &b->d_bar, 1, "batch grid barrier"));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_inst, inst.data(), sizeof(BInst) * B, cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BTile) * tiles.size(), cudaMemcpyHostToDevice, st));
   PAT_TRY_CUDA(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
@@ -172,11 +177,28 @@ BatchStepArgs step_args(const pat_batch* b, int t, bool adjoint) {
   return a;
 }
 
+// Steps 0 .. T-1 of K or K*: one launch per step, or all of them in one
+// cooperative launch with a grid barrier between steps (b->runall).
+pat_status batch_steps(pat_batch* b, int T, bool adjoint, cudaStream_t st) {
+  const int nctas = adjoint ? b->nctas_adj : b->nctas;
+  if (b->runall) {
+    if (T <= 0) return PAT_OK;
+    PAT_TRY_CUDA(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), st));
+    BatchStepArgs a = step_args(b, 0, adjoint);
+    a.t_end = T;
+    a.active_dev = b->d_active;
+    a.bar = b->d_bar;
+    PAT_TRY_CUDA(batch_run_launch(b->R, b->variant, a, nctas, st));
+    return PAT_OK;
+  }
+  for (int t = 0; t < T; ++t) PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, adjoint), nctas, st));
+  return PAT_OK;
+}
+
 // K of every instance: the plans' image buffers -> the plans' sensor-data buffers.
 pat_status batch_forward(pat_batch* b, cudaStream_t st, int steps = -1) {
   const int T = steps < 0 ? b->max_nt : std::min(steps, b->max_nt);
-  for (int t = 0; t < T; ++t) PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, false), b->nctas, st));
-  return PAT_OK;
+  return batch_steps(b, T, false, st);
 }
 
 // K* of every instance: the plans' sensor-data buffers -> the plans' image buffers.
@@ -187,9 +209,7 @@ pat_status batch_adjoint(pat_batch* b, cudaStream_t st, int steps = -1) {
     PAT_TRY_CUDA(fill_launch(p->d_wv[2], p->N, 0.f, st));  // G = 0
   }
   const int T = steps < 0 ? b->max_nt : std::min(steps, b->max_nt);
-  for (int t = 0; t < T; ++t)
-    PAT_TRY_CUDA(batch_step_launch(b->R, b->variant, step_args(b, t, true), b->nctas_adj, st));
-  return PAT_OK;
+  return batch_steps(b, T, true, st);
 }
 
 // Autotuner: times the first steps of a batched K and of a batched K* with
@@ -197,9 +217,15 @@ pat_status batch_adjoint(pat_batch* b, cudaStream_t st, int steps = -1) {
 // with twice as many CTAs in flight; the adjoint stages two boxes per tile, so
 // it fits fewer CTAs per SM than the forward).  PAT_BATCH_TILE_Y=64|32 fixes
 // the shape instead.
+pat_status tune_launch(pat_batch* b, cudaStream_t st);
+
 pat_status tune(pat_batch* b, cudaStream_t st) {
   const char* env = getenv("PAT_BATCH_TILE_Y");
-  if (env && (strcmp(env, "64") == 0 || strcmp(env, "32") == 0)) return build_tables(b, strcmp(env, "64") == 0 ? 0 : 1, st);
+  if (env && (strcmp(env, "64") == 0 || strcmp(env, "32") == 0)) {
+    PAT_TRY(build_tables(b, strcmp(env, "64") == 0 ? 0 : 1, st));
+    return tune_launch(b, st);
+  }
+  b->runall = 0;
   for (pat_plan* p : b->plans) {
     PAT_TRY_CUDA(fill_launch(p->d_img, p->N, 0.f, st));
     PAT_TRY_CUDA(fill_launch(p->d_ybuf, (long long)p->ns * p->nt, 0.f, st));
@@ -231,6 +257,49 @@ pat_status tune(pat_batch* b, cudaStream_t st) {
   PAT_TRY(rc);
   const int best = b->tune_ms[1] < b->tune_ms[0] ? 1 : 0;
   if (best != b->variant) PAT_TRY(build_tables(b, best, st));
+  return tune_launch(b, st);
+}
+
+// Launch form for the chosen tile shape: the first steps of a batched K plus
+// K* timed as one launch per step and as one cooperative launch each (grid
+// barrier between steps); the faster is kept unless the caller fixed the form.
+pat_status tune_launch(pat_batch* b, cudaStream_t st) {
+  for (pat_plan* p : b->plans) {
+    PAT_TRY_CUDA(fill_launch(p->d_img, p->N, 0.f, st));
+    PAT_TRY_CUDA(fill_launch(p->d_ybuf, (long long)p->ns * p->nt, 0.f, st));
+  }
+  const int steps = std::min(b->max_nt, 48);
+  cudaEvent_t e0, e1;
+  PAT_TRY_CUDA(cudaEventCreate(&e0));
+  PAT_TRY_CUDA(cudaEventCreate(&e1));
+  pat_status rc = PAT_OK;
+  for (int ra = 0; ra < 2 && rc == PAT_OK; ++ra) {
+    b->runall = ra;
+    rc = batch_forward(b, st, 4);  // warm-up
+    if (rc != PAT_OK) break;
+    cudaEventRecord(e0, st);
+    rc = batch_forward(b, st, steps);
+    if (rc == PAT_OK) rc = batch_adjoint(b, st, steps);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      set_error("batched launch tuning failed: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = PAT_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->launch_ms[ra] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PAT_TRY(rc);
+  int status = 0;
+  PAT_TRY_CUDA(cudaMemcpy(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status != PAT_OK) {
+    set_error("batched kernel wait timed out while tuning");
+    return (pat_status)status;
+  }
+  b->runall = b->launch_req == 1 ? 0 : b->launch_req == 2 ? 1 : (b->launch_ms[1] < b->launch_ms[0] ? 1 : 0);
   return PAT_OK;
 }
 
@@ -357,6 +426,31 @@ void pat_batch_destroy(pat_batch* b) {
   if (b->cap) cudaStreamDestroy(b->cap);
   bfree_all(b);
   delete b;
+}
+
+pat_status pat_batch_launch(pat_batch* b, int mode, int* runall, double* ms) {
+  if (!b || mode < -1 || mode > 2) {
+    set_error("batch must not be NULL and mode in -1 .. 2");
+    return PAT_ERR_INVALID;
+  }
+  if (mode >= 0) {
+    b->launch_req = mode;
+    const int want = mode == 1 ? 0 : mode == 2 ? 1 : (b->launch_ms[1] < b->launch_ms[0] ? 1 : 0);
+    if (want != b->runall) {
+      b->runall = want;
+      if (b->graph) {  // the captured iteration holds the other launch form
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_nodes = 0;
+      }
+    }
+  }
+  if (runall) *runall = b->runall;
+  if (ms) {
+    ms[0] = b->launch_ms[0];
+    ms[1] = b->launch_ms[1];
+  }
+  return PAT_OK;
 }
 
 pat_status pat_batch_info(pat_batch* b, int* tile_rows, int* ctas, long long* graph_nodes, double* tune_ms) {

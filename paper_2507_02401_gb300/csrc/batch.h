@@ -46,6 +46,10 @@ struct BatchStepArgs {
   float w[kMaxR + 1];
   int* status;
   long long timeout_ns;
+  // whole-application launch (one cooperative launch for every step):
+  int t_end;                  // steps t .. t_end - 1; 0 for a one-step launch
+  const int* active_dev;      // active tiles per global step (device)
+  unsigned* bar;              // grid-barrier arrival counter, zero at launch
 };
 
 constexpr int BATCH_MAPS = 5;
@@ -58,6 +62,9 @@ int batch_tile_y(int variant);  // tile height of a kernel variant (0: 64 rows, 
 size_t batch_smem(int R, int variant, bool adj);
 int batch_max_ctas(int R, int variant, bool adj);  // co-resident CTAs on this device
 cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st);
+// All steps a.t .. a.t_end - 1 in one cooperative launch of nctas co-resident CTAs,
+// a bounded grid-wide barrier between steps (a.bar zeroed beforehand).
+cudaError_t batch_run_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st);
 cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map);
 
 }  // namespace pat
@@ -71,6 +78,11 @@ struct pat_batch {
   pat::BTile* d_tiles = nullptr;
   CUtensorMap* d_maps = nullptr;
   int* d_status = nullptr;       // timeout of a bounded wait in the batched kernel
+  int* d_active = nullptr;       // active[] in device memory (run-all launches)
+  unsigned* d_bar = nullptr;     // grid-barrier counter of a run-all launch
+  int runall = 0;                // 1: K / K* as one cooperative launch each; 0: one launch per time step
+  int launch_req = 0;            // 0: the autotuner chooses; 1: per step; 2: one launch per application
+  double launch_ms[2] = {0, 0};  // autotuner: per-step launches, one launch (first steps of K plus K*)
   long long timeout_ns = 2000000000LL;
   std::vector<void*> allocations;
   cudaStream_t cap = nullptr;    // capture stream

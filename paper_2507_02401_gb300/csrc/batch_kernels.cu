@@ -22,6 +22,7 @@
 // ranges) is read two tiles ahead of its use, so the only loads left between
 // the end of one tile and the stencil of the next are the tile's own D cells
 // and the TMA boxes issued one tile ahead.
+#include <algorithm>
 #include <mutex>
 
 #include "batch.h"
@@ -48,7 +49,37 @@ struct GB {
   static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
 };
 
-template <int R, int TY, bool ADJ>
+// Grid-wide barrier of a cooperative launch: every CTA arrives once per
+// barrier on a monotonic counter and waits (bounded) until all gridDim.x CTAs
+// of barrier `round` (1, 2, ...) have arrived.  Thread 0 releases the CTA's
+// global writes before arriving and, after the acquire, fences the async proxy
+// so that the TMA loads it issues next see the other CTAs' writes.  False when
+// the wait gave up (timeout, or another CTA recorded a failure in `status`).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned round, int* status, long long timeout_ns) {
+  __syncthreads();
+  int fail = 0;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const unsigned target = round * gridDim.x;
+    const unsigned long long t0 = global_timer_ns();
+    for (unsigned it = 0;; ++it) {
+      if (ld_acquire_gpu_u(bar) >= target) break;
+      if ((it & 63u) == 63u) {
+        if (ld_relaxed_gpu(status) != (int)PAT_OK || (long long)(global_timer_ns() - t0) > timeout_ns ||
+            it > (1u << 30)) {
+          atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
+          fail = 1;
+          break;
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  return __syncthreads_or(fail) == 0;
+}
+
+template <int R, int TY, bool ADJ, bool RUNALL>
 __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(const BatchStepArgs a) {
   using G = GB<R, TY, ADJ>;
   constexpr int THREADS = G::THREADS, RUN = G::RUN;
@@ -58,7 +89,6 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
 
   const int t = threadIdx.x;
   const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * RUN;
-  const int step = a.t;
 
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -67,6 +97,16 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
   }
   __syncthreads();
 
+  int k = 0, issued = 0;  // tiles processed (stage k & 1, phase (k >> 1) & 1) and TMA pairs issued, over all steps
+  bool ok = true;
+  const int t_end = RUNALL ? a.t_end : a.t + 1;
+  for (int step = a.t; step < t_end && ok; ++step) {
+  if (RUNALL && step > a.t && !grid_barrier(a.bar, (unsigned)(step - a.t), a.status, a.timeout_ns)) {
+    ok = false;
+    break;
+  }
+  const int active = RUNALL ? __ldg(a.active_dev + step) : a.active;
+
   // tile descriptor in registers: instance, origin and the list range of this direction
   // (an empty descriptor past the active prefix)
   struct Desc {
@@ -74,7 +114,7 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
   };
   auto desc = [&](int tile) {
     Desc d{0, 0, 0, 0, 0};
-    if (tile < a.active) {
+    if (tile < active) {
       const int4* p = reinterpret_cast<const int4*>(a.tiles + tile);
       const int4 u = __ldg(p), v = __ldg(p + 1);
       d = Desc{u.x, u.y, u.z, ADJ ? v.z : v.x, ADJ ? v.w : v.y};
@@ -90,17 +130,18 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
     if (ADJ) tma_load_2d(st + G::PBOX, maps + 3 + (step & 1), d.gx0 - XH, d.gy0 - R, &bars[s]);
   };
   Desc dc = desc(blockIdx.x), dn = desc(blockIdx.x + gridDim.x);
-  if (t == 0 && (int)blockIdx.x < a.active) issue(dc, 0);
+  if ((int)blockIdx.x < active) {
+    if (t == 0) issue(dc, k & 1);
+    ++issued;
+  }
 
-  int k = 0, issued = ((int)blockIdx.x < a.active) ? 1 : 0;
-  bool ok = true;
-  for (int tile = blockIdx.x; tile < a.active; tile += gridDim.x, ++k) {
+  for (int tile = blockIdx.x; tile < active; tile += gridDim.x, ++k) {
     const int s = k & 1;
     const int nxt = tile + gridDim.x;
     const Desc dnn = desc(nxt + gridDim.x);  // consumed two tiles from now
     if (t == 0) {
       fence_proxy_async_shared();  // the other stage was last read through the generic proxy
-      if (nxt < a.active) {
+      if (nxt < active) {
         issue(dn, s ^ 1);
         ++issued;
       }
@@ -206,24 +247,28 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
     dc = dn;
     dn = dnn;
   }
+  }  // steps
   // after a timed-out wait: give the copies in flight a bounded chance to land
   if (t == 0 && !ok)
     for (int j = max(0, issued - 2); j < issued; ++j) mbar_wait(&bars[j & 1], (j >> 1) & 1, a.timeout_ns);
 }
 
 template <int R, int TY>
-const void* kernel_ptr(bool adj) {
-  return adj ? reinterpret_cast<const void*>(&batch_step_kernel<R, TY, true>)
-             : reinterpret_cast<const void*>(&batch_step_kernel<R, TY, false>);
+const void* kernel_ptr(bool adj, bool runall) {
+  if (runall)
+    return adj ? reinterpret_cast<const void*>(&batch_step_kernel<R, TY, true, true>)
+               : reinterpret_cast<const void*>(&batch_step_kernel<R, TY, false, true>);
+  return adj ? reinterpret_cast<const void*>(&batch_step_kernel<R, TY, true, false>)
+             : reinterpret_cast<const void*>(&batch_step_kernel<R, TY, false, false>);
 }
 
-const void* kernel_for(int R, int variant, bool adj) {
+const void* kernel_for(int R, int variant, bool adj, bool runall = false) {
   const bool tall = variant == 0;
   switch (R) {
-    case 1: return tall ? kernel_ptr<1, 64>(adj) : kernel_ptr<1, 32>(adj);
-    case 3: return tall ? kernel_ptr<3, 64>(adj) : kernel_ptr<3, 32>(adj);
-    case 5: return tall ? kernel_ptr<5, 64>(adj) : kernel_ptr<5, 32>(adj);
-    case 7: return tall ? kernel_ptr<7, 64>(adj) : kernel_ptr<7, 32>(adj);
+    case 1: return tall ? kernel_ptr<1, 64>(adj, runall) : kernel_ptr<1, 32>(adj, runall);
+    case 3: return tall ? kernel_ptr<3, 64>(adj, runall) : kernel_ptr<3, 32>(adj, runall);
+    case 5: return tall ? kernel_ptr<5, 64>(adj, runall) : kernel_ptr<5, 32>(adj, runall);
+    case 7: return tall ? kernel_ptr<7, 64>(adj, runall) : kernel_ptr<7, 32>(adj, runall);
     default: return nullptr;
   }
 }
@@ -239,21 +284,26 @@ size_t batch_smem(int R, int variant, bool adj) {
 }
 
 int batch_max_ctas(int R, int variant, bool adj) {
-  const void* fn = kernel_for(R, variant, adj);
-  if (!fn) return 0;
-  const size_t smem = batch_smem(R, variant, adj);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  // co-resident CTAs of the per-step and of the run-all kernel alike (the smaller of the two)
+  int best = -1;
+  for (int runall = 0; runall < 2; ++runall) {
+    const void* fn = kernel_for(R, variant, adj, runall != 0);
+    if (!fn) return 0;
+    const size_t smem = batch_smem(R, variant, adj);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_for(variant, adj), smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = best < 0 ? per * sms : std::min(best, per * sms);
   }
-  int dev = 0, sms = 0, per = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads_for(variant, adj), smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return per * sms;
+  return best;
 }
 
 cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st) {
@@ -264,6 +314,25 @@ cudaError_t batch_step_launch(int R, int variant, const BatchStepArgs& a, int nc
   const int grid = nctas < a.active ? nctas : a.active;
   void* args[] = {const_cast<BatchStepArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(threads_for(variant, adj)), args, batch_smem(R, variant, adj), st);
+}
+
+cudaError_t batch_run_launch(int R, int variant, const BatchStepArgs& a, int nctas, cudaStream_t st) {
+  if (a.t_end <= a.t) return cudaSuccess;
+  const bool adj = a.adjoint != 0;
+  const void* fn = kernel_for(R, variant, adj, true);
+  if (!fn || nctas <= 0) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(threads_for(variant, adj));
+  cfg.dynamicSmemBytes = batch_smem(R, variant, adj);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA co-resident: the grid barrier cannot deadlock
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<BatchStepArgs*>(&a)};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t batch_encode(const float* base, int nx, int ny, int R, int variant, CUtensorMap* map) {

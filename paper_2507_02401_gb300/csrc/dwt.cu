@@ -7,10 +7,16 @@
 //   a_k = sum_j h_j x[(2k+j) mod n],  d_k = sum_j g_j x[(2k+j) mod n];
 // synthesis is the transpose: x[(2k+j) mod n] += h_j a_k + g_j d_k.
 //
-// 2D levels are fused: one CTA loads a periodic input window into shared
+// 2D levels are fused: one CTA stages a periodic input window in shared
 // memory, filters along x, then along y, and writes the four bands (details
-// times the level weight).  3D levels run as separable 1D passes.
+// times the level weight).  Levels whose width is a multiple of 8 take the
+// HBM-rate kernels (16-byte cp.async staging with the periodic wrap computed
+// per 16-byte chunk, float4 band stores); narrower levels take the generic
+// kernels.  3D levels with width a multiple of 8 run as one fused pass
+// (x/y in shared memory, z from a register ring while marching through z);
+// other 3D levels run as separable 1D passes.
 #include "internal.h"
+#include "tma.cuh"
 
 namespace pat {
 namespace {
@@ -138,6 +144,462 @@ __global__ void __launch_bounds__(S_THREADS) dwt2d_synthesis_kernel(const float*
   }
 }
 
+
+// ------------------------------------------- 2D levels at HBM rate (nx % 8 == 0)
+// 16-byte asynchronous copy global -> shared, cached in L2 only
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ float4 f4fma(float w, const float4& v, const float4& a) {
+  return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
+}
+__device__ __forceinline__ float4 f4scale(float w, const float4& v) {
+  return make_float4(w * v.x, w * v.y, w * v.z, w * v.w);
+}
+
+// Analysis: a CTA makes OX x OY coefficients of each band from the input window
+// rows [2 ky0, 2 ky0 + 2 OY + L - 2) x columns [2 kx0, 2 kx0 + 2 OX + HX) (periodic).
+template <int L>
+struct A2F {
+  static constexpr int OX = 64, OY = 16, THREADS = 256;
+  static constexpr int HX = (L - 2 + 3) / 4 * 4;  // right halo, rounded up to whole float4
+  static constexpr int WX = 2 * OX + HX;
+  static constexpr int WY = 2 * OY + L - 2;
+  static constexpr int NQ = WX / 4;
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt2d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny,
+                                                                  float* __restrict__ A, float* __restrict__ Hb,
+                                                                  float* __restrict__ Vb, float* __restrict__ Db,
+                                                                  float wdet, const Filt f) {
+  using G = A2F<L>;
+  __shared__ __align__(16) float win[G::WY][G::WX];
+  __shared__ __align__(16) float lo[G::WY][G::OX];
+  __shared__ __align__(16) float hi[G::WY][G::OX];
+  const int t = threadIdx.x;
+  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
+  for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+    const int r = i / G::NQ, q = i % G::NQ;
+    const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles the wrap
+    cp_async16(&win[r][4 * q], in + (long long)gy * nx + gx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // along x: outputs 4q .. 4q+3 of window row r read window columns 8q .. 8q + 6 + L - 1
+  for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {
+    const int r = i / (G::OX / 4), q = i % (G::OX / 4);
+    float v[8 + G::HX];
+#pragma unroll
+    for (int c = 0; c < (8 + G::HX) / 4; ++c) {
+      const float4 w4 = *reinterpret_cast<const float4*>(&win[r][8 * q + 4 * c]);
+      v[4 * c] = w4.x;
+      v[4 * c + 1] = w4.y;
+      v[4 * c + 2] = w4.z;
+      v[4 * c + 3] = w4.w;
+    }
+    float sl[4], sh[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sl[k] = 0.f;
+      sh[k] = 0.f;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        sl[k] = fmaf(f.h[j], v[2 * k + j], sl[k]);
+        sh[k] = fmaf(f.g[j], v[2 * k + j], sh[k]);
+      }
+    }
+    *reinterpret_cast<float4*>(&lo[r][4 * q]) = make_float4(sl[0], sl[1], sl[2], sl[3]);
+    *reinterpret_cast<float4*>(&hi[r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+  }
+  __syncthreads();
+  // along y: 4 consecutive coefficients of one output row per thread
+  const int qx = t % (G::OX / 4), ky = t / (G::OX / 4);
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), hh = a, vv = a, dd = a;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float4 l = *reinterpret_cast<const float4*>(&lo[2 * ky + j][4 * qx]);
+    const float4 h = *reinterpret_cast<const float4*>(&hi[2 * ky + j][4 * qx]);
+    a = f4fma(f.h[j], l, a);
+    hh = f4fma(f.g[j], l, hh);  // x low, y high
+    vv = f4fma(f.h[j], h, vv);  // x high, y low
+    dd = f4fma(f.g[j], h, dd);
+  }
+  const int nx2 = nx >> 1, oy = ky0 + ky, ox = kx0 + 4 * qx;
+  if (oy < (ny >> 1) && ox < nx2) {  // nx2 % 4 == 0: the four coefficients are all in or all out
+    const long long o = (long long)oy * nx2 + ox;
+    *reinterpret_cast<float4*>(A + o) = a;
+    *reinterpret_cast<float4*>(Hb + o) = f4scale(wdet, hh);
+    *reinterpret_cast<float4*>(Vb + o) = f4scale(wdet, vv);
+    *reinterpret_cast<float4*>(Db + o) = f4scale(wdet, dd);
+  }
+}
+
+// Synthesis: a CTA makes the 2 OX x 2 OY pixels of coefficient block
+// (kx0 .. kx0+OX-1, ky0 .. ky0+OY-1) from the coefficient window rows
+// [ky0 - LH, ky0 + OY) x columns [kx0 - CX, kx0 + OX) of each band (periodic).
+template <int L>
+struct S2F {
+  static constexpr int OX = 64, OY = 16, THREADS = 256;
+  static constexpr int LH = L / 2 - 1;             // coefficients left of / above the block that reach it
+  static constexpr int CX = (LH + 3) / 4 * 4;      // left halo, rounded up to whole float4
+  static constexpr int WX = OX + CX;
+  static constexpr int WY = OY + LH;
+  static constexpr int NQ = WX / 4;
+  static constexpr int K0 = (CX - LH) & ~1;        // first (even) window column a pixel quad reads
+  static constexpr int NK2 = (CX + 2 - K0) / 2;    // float2 loads per pixel quad
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* __restrict__ A,
+                                                                   const float* __restrict__ Hb,
+                                                                   const float* __restrict__ Vb,
+                                                                   const float* __restrict__ Db, float wdet, int nx,
+                                                                   int ny, float* __restrict__ out, const Filt f) {
+  using G = S2F<L>;
+  __shared__ __align__(16) float cw[4][G::WY][G::WX];
+  __shared__ __align__(16) float lo[2 * G::OY][G::WX];
+  __shared__ __align__(16) float hi[2 * G::OY][G::WX];
+  const int t = threadIdx.x;
+  const int nx2 = nx >> 1, ny2 = ny >> 1;
+  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
+  for (int i = t; i < 4 * G::WY * G::NQ; i += G::THREADS) {
+    const int b = i / (G::WY * G::NQ), rq = i % (G::WY * G::NQ);
+    const int r = rq / G::NQ, q = rq % G::NQ;
+    // periodic (a coarse level may be shorter than the halo: wrap repeatedly); nx2 % 4 == 0
+    const int ky = pmod(ky0 - G::LH + r, ny2), kx = pmod(kx0 - G::CX + 4 * q, nx2);
+    const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
+    cp_async16(&cw[b][r][4 * q], src + (long long)ky * nx2 + kx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // along y: pixel row r of the block (row 2 ky0 + r) at every window column;
+  // x[2k + j] gets h_j a_k + g_j d_k, so row r reads window rows (r - j)/2 + LH, j = r mod 2, r mod 2 + 2, ...
+  // (each item is a row pair, so the filter taps of both parities are compile-time indices)
+  for (int i = t; i < G::OY * G::NQ; i += G::THREADS) {
+    const int rp = i / G::NQ, q = i % G::NQ;
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      const int r = 2 * rp + par;
+      float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sg = sa, sv = sa, sd = sa;
+#pragma unroll
+      for (int jj = 0; jj < L / 2; ++jj) {
+        const int j = 2 * jj + par;
+        const int k = rp - jj + G::LH;  // (r - j) / 2 + LH
+        sa = f4fma(f.h[j], *reinterpret_cast<const float4*>(&cw[0][k][4 * q]), sa);
+        sg = f4fma(f.g[j], *reinterpret_cast<const float4*>(&cw[1][k][4 * q]), sg);
+        sv = f4fma(f.h[j], *reinterpret_cast<const float4*>(&cw[2][k][4 * q]), sv);
+        sd = f4fma(f.g[j], *reinterpret_cast<const float4*>(&cw[3][k][4 * q]), sd);
+      }
+      // lo = sum h A + wdet sum g H;  hi = wdet (sum h V + sum g D)
+      *reinterpret_cast<float4*>(&lo[r][4 * q]) = make_float4(fmaf(wdet, sg.x, sa.x), fmaf(wdet, sg.y, sa.y),
+                                                              fmaf(wdet, sg.z, sa.z), fmaf(wdet, sg.w, sa.w));
+      *reinterpret_cast<float4*>(&hi[r][4 * q]) =
+          make_float4(wdet * (sv.x + sd.x), wdet * (sv.y + sd.y), wdet * (sv.z + sd.z), wdet * (sv.w + sd.w));
+    }
+  }
+  __syncthreads();
+  // along x: pixels 4p .. 4p+3 of row r; pixel i reads window columns (i - j)/2 + CX
+  for (int i = t; i < 2 * G::OY * (2 * G::OX / 4); i += G::THREADS) {
+    const int r = i / (2 * G::OX / 4), p = i % (2 * G::OX / 4);
+    float l[2 * G::NK2], h[2 * G::NK2];  // window columns 2p + K0 ..
+#pragma unroll
+    for (int c = 0; c < G::NK2; ++c) {
+      const float2 l2 = *reinterpret_cast<const float2*>(&lo[r][2 * p + G::K0 + 2 * c]);
+      const float2 h2 = *reinterpret_cast<const float2*>(&hi[r][2 * p + G::K0 + 2 * c]);
+      l[2 * c] = l2.x;
+      l[2 * c + 1] = l2.y;
+      h[2 * c] = h2.x;
+      h[2 * c + 1] = h2.y;
+    }
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      v[e] = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < L / 2; ++jj) {
+        const int j = 2 * jj + (e & 1);
+        const int k = ((e - j) >> 1) + G::CX - G::K0;  // index into l/h (window column - 2p - K0)
+        v[e] = fmaf(f.h[j], l[k], v[e]);
+        v[e] = fmaf(f.g[j], h[k], v[e]);
+      }
+    }
+    const int iy = 2 * ky0 + r, ix = 2 * kx0 + 4 * p;
+    if (iy < ny && ix < nx) *reinterpret_cast<float4*>(out + (long long)iy * nx + ix) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+
+// ----------------------------------------- 3D levels at HBM rate (nx % 8 == 0)
+// One pass per level: a CTA owns an OX x OY block of coefficient columns and
+// marches through a chunk of z planes.  Each input plane's window is staged
+// by cp.async (NSLOT - 1 planes ahead), filtered along x and y in shared
+// memory into the four (x, y) quarters; each thread keeps its quarter values
+// of the last L planes in registers and applies the z filter every second
+// plane, writing the eight bands (code = zb << 2 | yb << 1 | xb; code 0 is the
+// approximation) with float4 stores.
+struct Bands8 {
+  float* p[8];
+};
+struct CBands8 {
+  const float* p[8];
+};
+__device__ __forceinline__ const float* band_sel(const CBands8& b, int c) {
+  return c == 0 ? b.p[0] : c == 1 ? b.p[1] : c == 2 ? b.p[2] : c == 3 ? b.p[3]
+       : c == 4 ? b.p[4] : c == 5 ? b.p[5] : c == 6 ? b.p[6] : b.p[7];
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int L>
+struct A3F {
+  static constexpr int OX = 32, OY = 8, THREADS = 256, NSLOT = 4;
+  static constexpr int HX = (L - 2 + 3) / 4 * 4;
+  static constexpr int WX = 2 * OX + HX;
+  static constexpr int WY = 2 * OY + L - 2;
+  static constexpr int NQ = WX / 4;
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
+                                                                  const Bands8 out, float wdet, int cz, const Filt f) {
+  using G = A3F<L>;
+  __shared__ __align__(16) float slab[G::NSLOT][G::WY][G::WX];
+  __shared__ __align__(16) float xl[G::WY][G::OX];
+  __shared__ __align__(16) float xh[G::WY][G::OX];
+  const int t = threadIdx.x;
+  const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
+  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
+  const int kz1 = min(kz0 + cz, nz2);
+  const int nplanes = 2 * (kz1 - kz0) + L - 2;  // input planes 2 kz0 .. 2 kz1 + L - 3 (periodic)
+  auto load = [&](int pl) {
+    if (pl < nplanes) {
+      const long long zoff = (long long)((2 * kz0 + pl) % nz) * ny;
+      float* dst = &slab[pl % G::NSLOT][0][0];
+      for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+        const int r = i / G::NQ, q = i % G::NQ;
+        const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;
+        cp_async16(dst + r * G::WX + 4 * q, in + (zoff + gy) * nx + gx);
+      }
+    }
+    cp_async_commit();  // one group per plane (possibly empty) keeps the group count uniform
+  };
+#pragma unroll
+  for (int pl = 0; pl < G::NSLOT - 1; ++pl) load(pl);
+  // this thread's y-pass output: quarter qq (xb = qq & 1, yb = qq >> 1), row ky, columns 4 qx .. 4 qx + 3
+  const int qq = t / 64, ky = (t / 8) % 8, qx = t % 8;
+  const int xb = qq & 1, yb = qq >> 1;
+  float4 ring[L];  // quarter values of the last L planes, oldest first
+#pragma unroll
+  for (int j = 0; j < L; ++j) ring[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int pl = 0; pl < nplanes; ++pl) {
+    load(pl + G::NSLOT - 1);
+    cp_async_wait_group<G::NSLOT - 1>();  // this thread's copies of plane pl have landed
+    __syncthreads();                      // ... and every other thread's
+    const float(*w)[G::WX] = slab[pl % G::NSLOT];
+    for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {  // along x
+      const int r = i / (G::OX / 4), q = i % (G::OX / 4);
+      float v[8 + G::HX];
+#pragma unroll
+      for (int c = 0; c < (8 + G::HX) / 4; ++c) {
+        const float4 w4 = *reinterpret_cast<const float4*>(&w[r][8 * q + 4 * c]);
+        v[4 * c] = w4.x;
+        v[4 * c + 1] = w4.y;
+        v[4 * c + 2] = w4.z;
+        v[4 * c + 3] = w4.w;
+      }
+      float sl[4], sh[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sl[k] = 0.f;
+        sh[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+          sl[k] = fmaf(f.h[j], v[2 * k + j], sl[k]);
+          sh[k] = fmaf(f.g[j], v[2 * k + j], sh[k]);
+        }
+      }
+      *reinterpret_cast<float4*>(&xl[r][4 * q]) = make_float4(sl[0], sl[1], sl[2], sl[3]);
+      *reinterpret_cast<float4*>(&xh[r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+    }
+    __syncthreads();
+    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);  // along y
+    const float(*src)[G::OX] = xb ? xh : xl;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      v4 = f4fma(yb ? f.g[j] : f.h[j], *reinterpret_cast<const float4*>(&src[2 * ky + j][4 * qx]), v4);
+#pragma unroll
+    for (int j = 0; j < L - 1; ++j) ring[j] = ring[j + 1];
+    ring[L - 1] = v4;
+    if (pl >= L - 1 && ((pl - (L - 1)) & 1) == 0) {  // ring = input planes 2m .. 2m + L - 1: output plane m
+      const int kz = kz0 + ((pl - (L - 1)) >> 1);
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        lo = f4fma(f.h[j], ring[j], lo);
+        hi = f4fma(f.g[j], ring[j], hi);
+      }
+      const int oy = ky0 + ky, ox = kx0 + 4 * qx;
+      if (oy < ny2 && ox < nx2) {
+        const long long o = ((long long)kz * ny2 + oy) * nx2 + ox;
+        float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
+        float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
+        *reinterpret_cast<float4*>(plo + o) = qq == 0 ? lo : f4scale(wdet, lo);
+        *reinterpret_cast<float4*>(phi + o) = f4scale(wdet, hi);
+      }
+    }
+  }
+}
+
+template <int L>
+struct S3F {
+  static constexpr int OX = 32, OY = 8, THREADS = 256, NSLOT = 3;  // coefficient block; 2 OX x 2 OY pixels
+  static constexpr int LH = L / 2 - 1;
+  static constexpr int CX = (LH + 3) / 4 * 4;
+  static constexpr int WX = OX + CX;
+  static constexpr int WY = OY + LH;
+  static constexpr int NQ = WX / 4;
+  static constexpr int K0 = (CX - LH) & ~1;
+  static constexpr int NK2 = (CX + 2 - K0) / 2;
+};
+
+// Synthesis of one 3D level: coefficient extents (nx/2, ny/2, nz/2) -> (nx, ny, nz).
+// Per coefficient plane m the x/y synthesis of the four zb = 0 bands and of the
+// four zb = 1 bands gives two full-resolution planes P_lo(m), P_hi(m); output
+// plane 2m + e is then sum_jj h_{2jj+e} P_lo(m - jj) + g_{2jj+e} P_hi(m - jj).
+template <int L>
+__global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
+                                                                   int nz, float* __restrict__ out, int cz,
+                                                                   const Filt f) {
+  using G = S3F<L>;
+  __shared__ __align__(16) float cw[G::NSLOT][8][G::WY][G::WX];
+  __shared__ __align__(16) float yl[2][2 * G::OY][G::WX];
+  __shared__ __align__(16) float yh[2][2 * G::OY][G::WX];
+  const int t = threadIdx.x;
+  const int cx = nx >> 1, cy = ny >> 1, cz2 = nz >> 1;
+  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
+  const int kz1 = min(kz0 + cz, cz2);
+  const int nplanes = kz1 - kz0 + G::LH;  // coefficient planes kz0 - LH .. kz1 - 1 (periodic)
+  auto load = [&](int pl) {
+    if (pl < nplanes) {
+      const long long zoff = (long long)pmod(kz0 - G::LH + pl, cz2) * cy;
+      for (int i = t; i < 8 * G::WY * G::NQ; i += G::THREADS) {
+        const int b = i / (G::WY * G::NQ), rq = i % (G::WY * G::NQ);
+        const int r = rq / G::NQ, q = rq % G::NQ;
+        const int ky = pmod(ky0 - G::LH + r, cy), kx = pmod(kx0 - G::CX + 4 * q, cx);
+        cp_async16(&cw[pl % G::NSLOT][b][r][4 * q], band_sel(in, b) + (zoff + ky) * cx + kx);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int pl = 0; pl < G::NSLOT - 1; ++pl) load(pl);
+  const int pr = t / 16, pq = t % 16;  // this thread's pixel row and quad (x-pass, z-pass, store)
+  float4 rlo[L / 2], rhi[L / 2];       // P_lo, P_hi of the last L/2 coefficient planes, oldest first
+#pragma unroll
+  for (int j = 0; j < L / 2; ++j) rlo[j] = rhi[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int pl = 0; pl < nplanes; ++pl) {
+    load(pl + G::NSLOT - 1);
+    cp_async_wait_group<G::NSLOT - 1>();
+    __syncthreads();
+    const float(*W)[G::WY][G::WX] = cw[pl % G::NSLOT];
+    // along y, both z halves: item = (half, row pair, quad)
+    for (int i = t; i < 2 * G::OY * G::NQ; i += G::THREADS) {
+      const int zb = i / (G::OY * G::NQ), rq = i % (G::OY * G::NQ);
+      const int rp = rq / G::NQ, q = rq % G::NQ;
+      const int c0 = zb << 2;
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;  // codes c0 | 0, 1, 2, 3
+#pragma unroll
+        for (int jj = 0; jj < L / 2; ++jj) {
+          const int j = 2 * jj + par;
+          const int k = rp - jj + G::LH;
+          s0 = f4fma(f.h[j], *reinterpret_cast<const float4*>(&W[c0 | 0][k][4 * q]), s0);
+          s2 = f4fma(f.g[j], *reinterpret_cast<const float4*>(&W[c0 | 2][k][4 * q]), s2);
+          s1 = f4fma(f.h[j], *reinterpret_cast<const float4*>(&W[c0 | 1][k][4 * q]), s1);
+          s3 = f4fma(f.g[j], *reinterpret_cast<const float4*>(&W[c0 | 3][k][4 * q]), s3);
+        }
+        const int r = 2 * rp + par;
+        // x-low rows: code c0 (weight 1 only for the approximation) + code c0|2; x-high rows: codes c0|1, c0|3
+        const float w0 = zb ? wdet : 1.f;
+        *reinterpret_cast<float4*>(&yl[zb][r][4 * q]) =
+            make_float4(fmaf(wdet, s2.x, w0 * s0.x), fmaf(wdet, s2.y, w0 * s0.y), fmaf(wdet, s2.z, w0 * s0.z),
+                        fmaf(wdet, s2.w, w0 * s0.w));
+        *reinterpret_cast<float4*>(&yh[zb][r][4 * q]) =
+            make_float4(wdet * (s1.x + s3.x), wdet * (s1.y + s3.y), wdet * (s1.z + s3.z), wdet * (s1.w + s3.w));
+      }
+    }
+    __syncthreads();
+    float4 P[2];  // along x: this thread's pixel quad of P_lo (zb = 0) and P_hi (zb = 1)
+#pragma unroll
+    for (int zb = 0; zb < 2; ++zb) {
+      float l[2 * G::NK2], h[2 * G::NK2];
+#pragma unroll
+      for (int c = 0; c < G::NK2; ++c) {
+        const float2 l2 = *reinterpret_cast<const float2*>(&yl[zb][pr][2 * pq + G::K0 + 2 * c]);
+        const float2 h2 = *reinterpret_cast<const float2*>(&yh[zb][pr][2 * pq + G::K0 + 2 * c]);
+        l[2 * c] = l2.x;
+        l[2 * c + 1] = l2.y;
+        h[2 * c] = h2.x;
+        h[2 * c + 1] = h2.y;
+      }
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[e] = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < L / 2; ++jj) {
+          const int j = 2 * jj + (e & 1);
+          const int k = ((e - j) >> 1) + G::CX - G::K0;
+          v[e] = fmaf(f.h[j], l[k], v[e]);
+          v[e] = fmaf(f.g[j], h[k], v[e]);
+        }
+      }
+      P[zb] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+#pragma unroll
+    for (int j = 0; j < L / 2 - 1; ++j) {
+      rlo[j] = rlo[j + 1];
+      rhi[j] = rhi[j + 1];
+    }
+    rlo[L / 2 - 1] = P[0];
+    rhi[L / 2 - 1] = P[1];
+    if (pl >= G::LH) {  // rings hold coefficient planes m - LH .. m: output planes 2m, 2m + 1
+      const int m = kz0 + pl - G::LH;
+      const int iy = 2 * ky0 + pr, ix = 2 * kx0 + 4 * pq;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < L / 2; ++jj) {
+          const int j = 2 * jj + e;
+          v = f4fma(f.h[j], rlo[L / 2 - 1 - jj], v);
+          v = f4fma(f.g[j], rhi[L / 2 - 1 - jj], v);
+        }
+        if (iy < ny && ix < nx)
+          *reinterpret_cast<float4*>(out + ((long long)(2 * m + e) * ny + iy) * nx + ix) = v;
+      }
+    }
+  }
+}
+
+// z planes per CTA for a level with coefficient-column count `cols` and
+// nz2 coefficient planes: chunks of 16 planes, halved (down to 4) until the
+// grid has at least three CTAs per SM.
+int chunk3d(long long cols, int nz2) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int cz = 16;
+  while (cz > 4 && cols * ((nz2 + cz - 1) / cz) < 3LL * sms) cz >>= 1;
+  return cz < nz2 ? cz : nz2;
+}
+
 // ------------------------------------------------- separable 1D (3D grids)
 // Array extents (n0 = fastest, n1, n2).  Analysis halves extent `axis`.
 __global__ void dwt1d_analysis_kernel(const float* __restrict__ in, int n0, int n1, int n2, int axis,
@@ -224,6 +686,14 @@ int grid1d(long long n) {
 cudaError_t dwt2d_analysis_level(const float* in, int nx, int ny, float* approx, float* bandH, float* bandV,
                                  float* bandD, float wdet, const float* h, const float* g, int L, cudaStream_t st) {
   const Filt f = make_filt(h, g, L);
+  if (nx % 8 == 0 && ny % 2 == 0 && aligned16(in) && aligned16(approx) && aligned16(bandH) && aligned16(bandV) &&
+      aligned16(bandD) && (L == 2 || L == 4 || L == 8)) {
+    dim3 grid(((nx >> 1) + 63) / 64, ((ny >> 1) + 15) / 16);
+    if (L == 2) dwt2d_analysis_fast_kernel<2><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
+    if (L == 4) dwt2d_analysis_fast_kernel<4><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
+    if (L == 8) dwt2d_analysis_fast_kernel<8><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
+    return cudaGetLastError();
+  }
   dim3 grid(((nx >> 1) + A_OX - 1) / A_OX, ((ny >> 1) + A_OY - 1) / A_OY);
   dwt2d_analysis_kernel<<<grid, A_THREADS, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
   return cudaGetLastError();
@@ -233,6 +703,14 @@ cudaError_t dwt2d_synthesis_level(const float* approx, const float* bandH, const
                                   float wdet, int nx, int ny, float* out, const float* h, const float* g, int L,
                                   cudaStream_t st) {
   const Filt f = make_filt(h, g, L);
+  if (nx % 8 == 0 && ny % 2 == 0 && aligned16(approx) && aligned16(bandH) && aligned16(bandV) && aligned16(bandD) &&
+      aligned16(out) && (L == 2 || L == 4 || L == 8)) {
+    dim3 grid(((nx >> 1) + 63) / 64, ((ny >> 1) + 15) / 16);
+    if (L == 2) dwt2d_synthesis_fast_kernel<2><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
+    if (L == 4) dwt2d_synthesis_fast_kernel<4><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
+    if (L == 8) dwt2d_synthesis_fast_kernel<8><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
+    return cudaGetLastError();
+  }
   dim3 grid((nx + S_OX - 1) / S_OX, (ny + S_OY - 1) / S_OY);
   dwt2d_synthesis_kernel<<<grid, S_THREADS, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
   return cudaGetLastError();
@@ -255,6 +733,46 @@ cudaError_t dwt1d_analysis_axis(const float* in, int n0, int n1, int n2, int axi
   m[axis] >>= 1;
   dwt1d_analysis_kernel<<<grid1d((long long)m[0] * m[1] * m[2]), 256, 0, st>>>(in, n0, n1, n2, axis, lo, hi, wlo,
                                                                                 whi, f);
+  return cudaGetLastError();
+}
+
+cudaError_t dwt3d_analysis_level(const float* in, int nx, int ny, int nz, float* const bands[8], float wdet,
+                                 const float* h, const float* g, int L, cudaStream_t st) {
+  if (nx % 8 != 0 || ny % 2 != 0 || nz % 2 != 0 || !(L == 2 || L == 4 || L == 8) || !aligned16(in))
+    return cudaErrorNotSupported;
+  Bands8 b;
+  for (int c = 0; c < 8; ++c) {
+    if (!aligned16(bands[c])) return cudaErrorNotSupported;
+    b.p[c] = bands[c];
+  }
+  const Filt f = make_filt(h, g, L);
+  const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
+  const long long cols = (long long)((nx2 + 31) / 32) * ((ny2 + 7) / 8);
+  const int cz = chunk3d(cols, nz2);
+  dim3 grid((nx2 + 31) / 32, (ny2 + 7) / 8, (nz2 + cz - 1) / cz);
+  if (L == 2) dwt3d_analysis_fast_kernel<2><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
+  if (L == 4) dwt3d_analysis_fast_kernel<4><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
+  if (L == 8) dwt3d_analysis_fast_kernel<8><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
+  return cudaGetLastError();
+}
+
+cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int nx, int ny, int nz, float* out,
+                                  const float* h, const float* g, int L, cudaStream_t st) {
+  if (nx % 8 != 0 || ny % 2 != 0 || nz % 2 != 0 || !(L == 2 || L == 4 || L == 8) || !aligned16(out))
+    return cudaErrorNotSupported;
+  CBands8 b;
+  for (int c = 0; c < 8; ++c) {
+    if (!aligned16(bands[c])) return cudaErrorNotSupported;
+    b.p[c] = bands[c];
+  }
+  const Filt f = make_filt(h, g, L);
+  const int cx = nx >> 1, cy = ny >> 1, cz2 = nz >> 1;
+  const long long cols = (long long)((cx + 31) / 32) * ((cy + 7) / 8);
+  const int cz = chunk3d(cols, cz2);
+  dim3 grid((cx + 31) / 32, (cy + 7) / 8, (cz2 + cz - 1) / cz);
+  if (L == 2) dwt3d_synthesis_fast_kernel<2><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
+  if (L == 4) dwt3d_synthesis_fast_kernel<4><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
+  if (L == 8) dwt3d_synthesis_fast_kernel<8><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
   return cudaGetLastError();
 }
 

@@ -190,6 +190,13 @@ cudaError_t dwt1d_analysis_axis(const float* in, int n0, int n1, int n2, int axi
                                 float whi, const float* h, const float* g, int L, cudaStream_t st);
 cudaError_t dwt1d_synthesis_axis(const float* lo, const float* hi, float wlo, float whi, int n0, int n1, int n2,
                                  int axis, float* out, const float* h, const float* g, int L, cudaStream_t st);
+// One fused 3D level (band pointers in code order zb << 2 | yb << 1 | xb, code 0 =
+// approximation); cudaErrorNotSupported (nothing launched) when nx % 8 != 0 or
+// an address is not 16-byte aligned, for the separable passes to take over.
+cudaError_t dwt3d_analysis_level(const float* in, int nx, int ny, int nz, float* const bands[8], float wdet,
+                                 const float* h, const float* g, int L, cudaStream_t st);
+cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int nx, int ny, int nz, float* out,
+                                  const float* h, const float* g, int L, cudaStream_t st);
 cudaError_t scale_copy_launch(float* dst, const float* src, long long n, float w, cudaStream_t st);
 
 // cg.cu

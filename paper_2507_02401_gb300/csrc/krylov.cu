@@ -163,6 +163,26 @@ pat_status objective(pat_plan* p, const float* x, const float* u, const float* y
 
 }  // namespace
 
+// J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 (FP64 reductions) and, when
+// grad != nullptr, its gradient E_s* K* (K E_s u - y) + alpha u (FP32).
+pat_status objective_device(pat_plan* p, const float* y, double alpha, double s, const float* u, double* J,
+                            float* grad, cudaStream_t st) {
+  const long long N = p->N, M = (long long)p->ns * p->nt;
+  PAT_TRY(apply_Es(p, s, u, p->d_img, st));
+  PAT_TRY(wave_forward(p, p->d_img, p->d_ybuf, st));
+  PAT_TRY_CUDA(axpy(p->d_ybuf, y, -1.0, M, st));  // r = K E_s u - y
+  double rr = 0.0, uu = 0.0;
+  PAT_TRY(dot_host(p, p->d_ybuf, p->d_ybuf, M, false, &rr, st));
+  PAT_TRY(dot_host(p, u, u, N, false, &uu, st));
+  *J = 0.5 * rr + 0.5 * alpha * uu;
+  if (grad) {
+    PAT_TRY(wave_adjoint(p, p->d_ybuf, p->d_img, st));
+    PAT_TRY(apply_EsT(p, s, p->d_img, grad, st));
+    PAT_TRY_CUDA(axpy(grad, u, alpha, N, st));
+  }
+  return PAT_OK;
+}
+
 pat_status landweber_device(pat_plan* p, const float* y, double alpha, double s, int iters, double omega, float* u,
                             float* x, double* J, cudaStream_t st) {
   const long long N = p->N, M = (long long)p->ns * p->nt;

@@ -14,7 +14,9 @@
 // (it exists on every device that loads the library, for the life of the
 // process).  Host code cannot use the array's name as a device address, so
 // its address is looked up once per device with cudaGetSymbolAddress, with
-// that device current, the first time the entry point runs on it.
+// that device current, the first time the entry point runs on it.  The
+// cached address is not refreshed after cudaDeviceReset (which unloads the
+// module); calls after a reset of the device are not supported.
 #include <cmath>
 #include <mutex>
 
@@ -53,13 +55,21 @@ pat_status scratch_address(float** out) {
   return PAT_OK;
 }
 
-bool on_device(const void* ptr) {
+// True if `ptr` is device (or managed) memory of the current device: the
+// kernels run on the current device with that device's scratch, so an array
+// of another device would need peer access and is refused.
+bool on_current_device(const void* ptr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -83,9 +93,20 @@ extern "C" pat_status pat_EsT_noalloc(int nx, int ny, int family, int levels, in
               kMaxLevels);
     return PAT_ERR_INVALID;
   }
-  if (!std::isfinite(s) || !x || !u || !on_device(x) || !on_device(u)) {
-    set_error("pat_EsT_noalloc: s must be finite and x, u device arrays");
+  if (!std::isfinite(s) || !x || !u || !on_current_device(x) || !on_current_device(u)) {
+    set_error("pat_EsT_noalloc: s must be finite and x, u device arrays of the current device");
     return PAT_ERR_INVALID;
+  }
+  {
+    // level 1 reads x around each output through the periodic filter support
+    // while it writes the finest bands into u: overlapping arrays would mix them
+    const char* xb = reinterpret_cast<const char*>(x);
+    const char* ub = reinterpret_cast<const char*>(u);
+    const long long bytes = (long long)nx * ny * (long long)sizeof(float);
+    if (xb < ub + bytes && ub < xb + bytes) {
+      set_error("pat_EsT_noalloc: x and u overlap; they must be separate arrays");
+      return PAT_ERR_INVALID;
+    }
   }
   double hd[kMaxTaps];
   if (!daubechies_filter(family, hd)) {

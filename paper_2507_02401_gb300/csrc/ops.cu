@@ -376,14 +376,26 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
   }
   float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
   const float* in = x;
+  long long launched = 0;
   for (int i = 1; i <= m; ++i) {
     const int ex = p->n[0] >> (i - 1), ey = p->n[1] >> (i - 1), ez = p->n[2] >> (i - 1);
     float* approx = (i == m) ? u : tmp[i & 1];
     const float wd = level_weight(p, i, s);
+    cudaError_t fused = cudaErrorNotSupported;
+    if (p->dim == 3) {
+      float* bands[8] = {approx};
+      for (int c = 1; c < 8; ++c) bands[c] = u + band_offset(p, i, c - 1);
+      fused = dwt3d_analysis_level(in, ex, ey, ez, bands, wd, p->hf, p->gf, p->L, st);
+      if (fused != cudaErrorNotSupported) PAT_TRY_CUDA(fused);
+    }
     if (p->dim == 2) {
       PAT_TRY_CUDA(dwt2d_analysis_level(in, ex, ey, approx, u + band_offset(p, i, 0), u + band_offset(p, i, 1),
                                         u + band_offset(p, i, 2), wd, p->hf, p->gf, p->L, st));
+      launched += 1;
+    } else if (fused == cudaSuccess) {
+      launched += 1;
     } else {
+      launched += 7;
       const long long ni = (long long)ex * ey * ez;
       float* T1 = p->d_dwt_t1;  // x-pass: lo | hi (ni/2 each)
       float* T2 = p->d_dwt_t2;  // y-pass: 4 quarters, index xb | yb<<1
@@ -400,7 +412,7 @@ pat_status apply_EsT(pat_plan* p, double s, const float* x, float* u, cudaStream
     }
     in = approx;
   }
-  count_kernels(p, (long long)m * (p->dim == 2 ? 1 : 7));
+  count_kernels(p, launched);
   return PAT_OK;
 }
 
@@ -416,14 +428,26 @@ pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_
   }
   float* tmp[2] = {p->d_dwt_a, p->d_dwt_b};
   const float* approx = u;
+  long long launched = 0;
   for (int i = m; i >= 1; --i) {
     const int ex = p->n[0] >> (i - 1), ey = p->n[1] >> (i - 1), ez = p->n[2] >> (i - 1);
     float* out = (i == 1) ? x : tmp[i & 1];
     const float wd = level_weight(p, i, s);
+    cudaError_t fused = cudaErrorNotSupported;
+    if (p->dim == 3) {
+      const float* bands[8] = {approx};
+      for (int c = 1; c < 8; ++c) bands[c] = u + band_offset(p, i, c - 1);
+      fused = dwt3d_synthesis_level(bands, wd, ex, ey, ez, out, p->hf, p->gf, p->L, st);
+      if (fused != cudaErrorNotSupported) PAT_TRY_CUDA(fused);
+    }
     if (p->dim == 2) {
       PAT_TRY_CUDA(dwt2d_synthesis_level(approx, u + band_offset(p, i, 0), u + band_offset(p, i, 1),
                                          u + band_offset(p, i, 2), wd, ex, ey, out, p->hf, p->gf, p->L, st));
+      launched += 1;
+    } else if (fused == cudaSuccess) {
+      launched += 1;
     } else {
+      launched += 7;
       const long long ni = (long long)ex * ey * ez;
       float* T1 = p->d_dwt_t1;
       float* T2 = p->d_dwt_t2;
@@ -440,7 +464,7 @@ pat_status apply_Es(pat_plan* p, double s, const float* u, float* x, cudaStream_
     }
     approx = out;
   }
-  count_kernels(p, (long long)m * (p->dim == 2 ? 1 : 7));
+  count_kernels(p, launched);
   return PAT_OK;
 }
 
@@ -856,6 +880,27 @@ pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, dou
   PAT_TRY(landweber_device(plan, dy, alpha, s, iters, omega, du, dx, J, st));
   if (u) PAT_TRY(out_back(u, du, plan->N, hu, st));
   if (x) PAT_TRY(out_back(x, dx, plan->N, hx, st));
+  PAT_TRY_CUDA(cudaStreamSynchronize(st));
+  return PAT_OK;
+}
+
+pat_status pat_objective(pat_plan* plan, const float* y, double alpha, double s, const float* u, double* J,
+                         float* grad, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (!y || !u || !J || !(alpha >= 0.0) || !std::isfinite(alpha) || !std::isfinite(s)) {
+    set_error("y, u and J must not be NULL, alpha finite and >= 0, s finite");
+    return PAT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ny = (size_t)plan->ns * plan->nt;
+  const float *dy, *du;
+  float* dg;
+  bool hy, hu, hg;
+  PAT_TRY(in_arr(plan, 0, y, ny, &dy, &hy, st));
+  PAT_TRY(in_arr(plan, 1, u, plan->N, &du, &hu, st));
+  PAT_TRY(out_arr(plan, 2, grad, plan->N, &dg, &hg));
+  PAT_TRY(objective_device(plan, dy, alpha, s, du, J, dg, st));
+  if (grad) PAT_TRY(out_back(grad, dg, plan->N, hg, st));
   PAT_TRY_CUDA(cudaStreamSynchronize(st));
   return PAT_OK;
 }

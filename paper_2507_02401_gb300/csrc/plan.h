@@ -122,6 +122,9 @@ pat_status kappa_grad_device(pat_plan* p, const float* x, const float* r, float*
 bool fourier_supported(int dim, int nx, int ny);
 pat_status fourier_setup(pat_plan* p, double length_cells, cudaStream_t st);
 pat_status fourier_apply(pat_plan* p, double s, const float* in, float* out, cudaStream_t st);
+// J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 into *J (host) and, if grad, its gradient (device, N).
+pat_status objective_device(pat_plan* p, const float* y, double alpha, double s, const float* u, double* J,
+                            float* grad, cudaStream_t st);
 pat_status landweber_device(pat_plan* p, const float* y, double alpha, double s, int iters, double omega, float* u,
                             float* x, double* J, cudaStream_t st);
 pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int iters, float* x, double* res,

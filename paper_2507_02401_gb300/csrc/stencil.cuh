@@ -80,6 +80,66 @@ __device__ __forceinline__ void lap_2x4(const float* __restrict__ S, int pitch, 
   }
 }
 
+// ------------------------------------------------ packed FP32x2 arithmetic
+// Blackwell issues two FP32 lanes per instruction (FADD2 / FFMA2 / FMUL2);
+// each lane rounds exactly as the scalar instruction does.  A pair term in
+// this form, fma(c, -2, a + b), equals (a + b) - 2c rounded once, i.e. the
+// scalar pair form bit for bit.
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Pair-form Laplacian of a 2 (rows) x 4 (cols) block as four packed pairs,
+// L[rr][p] = cells (2p, 2p+1) of row rr; same operand order as lap_2x4<R,
+// false, false> (y taps, then x taps), so the results agree bit for bit.
+template <int R>
+__device__ __forceinline__ void lap_2x4_x2(const float* __restrict__ S, int pitch, int srow, int scol,
+                                           const float2 (&w2)[R + 1], float2 L[2][2]) {
+  const float2 m2 = dup2(-2.f);
+  float4 col[2 + 2 * R];
+#pragma unroll
+  for (int i = 0; i < 2 + 2 * R; ++i) col[i] = *reinterpret_cast<const float4*>(S + (srow - R + i) * pitch + scol);
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 c = p ? hi2(col[rr + R]) : lo2(col[rr + R]);
+      float2 acc = dup2(0.f);
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float2 a = p ? hi2(col[rr + R + m]) : lo2(col[rr + R + m]);
+        const float2 b = p ? hi2(col[rr + R - m]) : lo2(col[rr + R - m]);
+        acc = __ffma2_rn(w2[m], __ffma2_rn(c, m2, __fadd2_rn(a, b)), acc);
+      }
+      L[rr][p] = acc;
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    float f[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(S + (srow + rr) * pitch + scol - 8 + 4 * q);
+      f[4 * q + 0] = v.x;
+      f[4 * q + 1] = v.y;
+      f[4 * q + 2] = v.z;
+      f[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 c = make_float2(f[8 + 2 * p], f[9 + 2 * p]);
+      float2 acc = L[rr][p];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float2 a = make_float2(f[8 + 2 * p + m], f[9 + 2 * p + m]);
+        const float2 b = make_float2(f[8 + 2 * p - m], f[9 + 2 * p - m]);
+        acc = __ffma2_rn(w2[m], __ffma2_rn(c, m2, __fadd2_rn(a, b)), acc);
+      }
+      L[rr][p] = acc;
+    }
+  }
+}
+
 // 16-byte load of data read once per launch (streamed: no L1 allocation)
 __device__ __forceinline__ float4 ld_stream4(const float* p) {
   float4 v;

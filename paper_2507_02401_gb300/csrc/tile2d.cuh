@@ -39,9 +39,9 @@ __device__ __forceinline__ float stencil_cell(const float4 (&win)[2 * R + 1], co
 // Laplacian of the 4 x RUN cells a thread owns in a box (pitch BW floats, R halo rows above the tile,
 // the thread's columns at XH + c0): lo[rr][j] for row r0 + rr.  For the low part of a compensated
 // pair (a field of the order of the rounding error of its high part), so it takes the cheapest form,
-// sum_m w_m (a + b) - w_c c with the centre weight w_c = 4 sum_m w_m rounded once: 2 FP operations per
-// tap; the rounded w_c departs from a zero-sum stencil by a relative 2^-24 of a field that is itself
-// ~2^-24 of the state.
+// sum_m w_m (a + b) - w_c c with the centre weight w_c = 4 sum_m w_m summed in FP32 (R additions and
+// a multiply, so up to R + 1 roundings): 2 FP operations per tap; the rounded w_c departs from a
+// zero-sum stencil by a relative ~R 2^-24 of a field that is itself ~2^-24 of the state.
 template <int R, int RUN, int BW, int XH>
 __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r0, int c0,
                                             const float* __restrict__ w, float (&lo)[RUN][4]) {

@@ -152,8 +152,9 @@ class Plan:
 
 class Batch:
     """Many 2D constant-medium plans advanced together by the batched engine
-    (one launch per time step over all instances' tiles; tile height chosen
-    by the library's autotuner when the batch is created).  The plans must
+    (all instances' tiles in one table; tile height and launch form -- one
+    launch per time step, or one cooperative launch per K / K* -- chosen by
+    the library's autotuner when the batch is created).  The plans must
     outlive the batch and are not used concurrently with it."""
 
     def __init__(self, plans, stream=None):
@@ -176,7 +177,14 @@ class Batch:
 
     @property
     def info(self):
-        return _lib.pat_batch_info(self.handle)
+        d = _lib.pat_batch_info(self.handle)
+        runall, ms = _lib.pat_batch_launch(self.handle, -1)
+        d.update(launch="one per application" if runall else "one per step", launch_tune_ms=ms)
+        return d
+
+    def set_launch(self, mode):
+        """0: autotuner's choice, 1: one launch per time step, 2: one cooperative launch per K / K*."""
+        _lib.pat_batch_launch(self.handle, mode)
 
     def forward(self, xs, outs=None, stream=None):
         """[K_i x_i] for every instance; returns a list of (Ns_i, nt_i) tensors."""

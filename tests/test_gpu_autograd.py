@@ -41,6 +41,9 @@ def _check(w, ndir, seed, tol_grad=1e-5, tol_fd=1e-5):
     res = _oracle_J_parts(wave, wav, u0, y, s)
     g_ref = wav.EsT(wave.adjoint(res), s) + alpha * u0
     assert rel(g, g_ref) <= tol_grad
+    # the objective's value (library, FP64 reductions) against the oracle's
+    J_ref = 0.5 * float(np.sum(res * res)) + 0.5 * alpha * float(u0 @ u0)
+    assert abs(float(J) - J_ref) <= 1e-5 * J_ref
 
     # central differences of the FP64 objective; K is linear, so
     # K E_s (u +- eps d) = K E_s u +- eps K E_s d exactly (up to FP64 rounding)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import Wave, Wavelet, cg, normal_op, rhs
+from oracle import Wave, Wavelet, cg, cg_converged, normal_op, rhs
 
 
 def _small(n=16, nt=40, order=4, family=4, levels=2, ns=12, seed=3):
@@ -84,3 +84,21 @@ def test_noise_free_reconstruction_converges():
         errs.append(np.linalg.norm(x - w.x_true) / np.linalg.norm(w.x_true))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.05, errs
+
+
+def test_cg_converged_is_the_dense_minimiser():
+    """The converged solve (residual tolerance) reaches the dense direct
+    solution of the normal equations, and reports a true residual below the
+    tolerance; a plain fixed-count CG with fewer iterations does not."""
+    wave, wav, rng = _small(seed=6)
+    s, alpha = 2.0, 1e-3
+    y = rng.standard_normal((wave.ns, wave.nt))
+    Hd = _dense(normal_op(wave, wav, s, alpha), 256)
+    u_ref = np.linalg.solve(Hd, rhs(wave, wav, y, s))
+    u, x, k, rel_res = cg_converged(wave, wav, y, alpha, s, rtol=1e-11)
+    assert rel_res <= 1e-10
+    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-8
+    u5, _, _ = cg(wave, wav, y, alpha, s, 5)
+    assert np.linalg.norm(u5 - u_ref) / np.linalg.norm(u_ref) > 1e-4
+    assert k > 5
+
