@@ -771,6 +771,9 @@ def run_batch(args):
                                f"{iters} CG iterations each; one step = one batched solve of all instances",
                    "engine": "batched", "tile_rows": info["tile_rows"], "ctas": info["ctas"],
                    "autotune_ms": info["tune_ms"], "graph_nodes_per_iteration": info["graph_nodes"],
+                   "launch": info["launch"],
+                   "launch_tune_ms": {"one per step": info["launch_tune_ms"][0],
+                                      "one per application": info["launch_tune_ms"][1]},
                    "l2": "256 MiB buffer written before every step (inside the timed region)",
                    "parallelism": f"replicas x{world} (independent batches per rank)"},
         "solves_per_s": world * args.steps * n_inst / (t_ms / 1e3),
@@ -791,7 +794,7 @@ def run_batch(args):
         "clocks": clocks,
     }
     if rank == 0 and args.accuracy:
-        line["accuracy_vs_oracle"] = batch_accuracy(ws, plans, batch, iters)
+        line["accuracy_vs_oracle"] = batch_accuracy(ws, plans, batch, iters, ys, alphas)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -816,14 +819,15 @@ def oracle_lambda_max(wave, wav, s, iters=15, seed=0):
     return lam
 
 
-def batch_accuracy(ws, plans, batch, iters, n_max=192, n_conv=128):
+def batch_accuracy(ws, plans, batch, iters, ys_other, alphas_other, n_max=192, n_conv=128):
     """Accuracy of the batched and of the sequential (pat_solve) path against
     the FP64 oracle, on every instance of the batched workload with n <= n_max:
     data simulated by the oracle, alpha = alpha_rel * the oracle's lambda_max
     (the same absolute alpha on every side), the oracle's CG at the same
     iteration count and, for n <= n_conv, the oracle's converged minimiser
-    (CG to ||b - H u|| <= 1e-10 ||b||).  Instances above n_max keep their
-    GPU-simulated data (they run in the batch but are not compared)."""
+    (CG to ||b - H u|| <= 1e-10 ||b||).  Instances above n_max keep the
+    benchmark's data and alpha (ys_other, alphas_other: they run in the batch
+    but are not compared)."""
     import torch
 
     import oracle
@@ -847,9 +851,9 @@ def batch_accuracy(ws, plans, batch, iters, n_max=192, n_conv=128):
         ys[i], alphas[i], ref[i] = y, a, (x_o, conv)
     t_oracle = time.perf_counter() - t0
     # GPU: one batched solve of all instances, then pat_solve per compared instance
-    yb = [torch.as_tensor(ys[i] if i in ys else np.zeros((p.ns, p.nt)), dtype=torch.float32, device="cuda")
-          for i, p in enumerate(plans)]
-    ab = [alphas.get(i, ws[i].alpha[0]) for i in range(len(ws))]
+    yb = [torch.as_tensor(ys[i], dtype=torch.float32, device="cuda") if i in ys else ys_other[i]
+          for i in range(len(plans))]
+    ab = [alphas.get(i, alphas_other[i]) for i in range(len(ws))]
     ss = [w.s[0] for w in ws]
     xs = [torch.empty(w.shape, device="cuda") for w in ws]
     rc, per = _lib.pat_batch_solve(batch.handle, yb, ab, ss, iters, xs, torch.cuda.current_stream())
@@ -931,7 +935,9 @@ def run_dwt_sweep(args):
     """The wavelet kernels (E_s = W^T S_s synthesis and E_s* = S_s W analysis,
     periodic db4) on HBM-sized grids: each application timed alone with CUDA
     events on the launching stream, a 256 MiB L2 flush before each, against
-    the algorithmic bytes of dwt_bytes_per_cell."""
+    the algorithmic bytes of dwt_bytes_per_cell (each application replayed
+    from a captured CUDA graph, so that host-side call overhead stays out of
+    the timed region)."""
     import torch
     from paper_2507_02401_gb300 import Plan
     peak, peak_kind = peaks()
@@ -956,12 +962,20 @@ def run_dwt_sweep(args):
         for name, fn in (("EsT", lambda: plan.EsT(x, 1.0, out=u)), ("Es", lambda: plan.Es(u, 1.0, out=x))):
             for _ in range(args.warmup):
                 fn()
+            # the application's launches captured once as a CUDA graph, so that the timed region holds
+            # device work only (the Python and ctypes marshalling of a call costs tens of microseconds)
+            cs = torch.cuda.Stream()
+            cs.wait_stream(stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=cs):
+                fn()
+            torch.cuda.synchronize()
             ms = 0.0
             for _ in range(reps):
-                flush.zero_()
+                flush.zero_()  # ~40 us of device work: the replay below is enqueued before it ends
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                fn()
+                graph.replay()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms += e0.elapsed_time(e1)

@@ -32,8 +32,10 @@ def rhs(wave, wav, y, s):
     return wav.EsT(wave.adjoint(y), s).ravel()
 
 
-def cg(wave, wav, y, alpha, s, iters, u0=None):
-    """Returns (u, x, log) with log[k] = (rr_k, pq_k, a_k) per iteration."""
+def cg(wave, wav, y, alpha, s, iters, u0=None, snapshots=None):
+    """Returns (u, x, log) with log[k] = (rr_k, pq_k, a_k) per iteration.
+    With `snapshots` (iteration counts), returns (u, x, log, {k: x_k}) with
+    the image E_s u_k after k iterations of this same run."""
     H = normal_op(wave, wav, s, alpha)
     b = rhs(wave, wav, y, s)
     if u0 is None:
@@ -45,6 +47,7 @@ def cg(wave, wav, y, alpha, s, iters, u0=None):
     p = r.copy()
     rr = float(r @ r)
     log = []
+    snaps = {}
     for _ in range(iters):
         q = H(p)
         pq = float(p @ q)
@@ -57,6 +60,10 @@ def cg(wave, wav, y, alpha, s, iters, u0=None):
         log.append((rr, pq, a))
         p = r + (rr_new / rr) * p
         rr = rr_new
+        if snapshots is not None and len(log) in snapshots:
+            snaps[len(log)] = wav.Es(u, s)
+    if snapshots is not None:
+        return u, wav.Es(u, s), np.array(log), snaps
     return u, wav.Es(u, s), np.array(log)
 
 

@@ -15,7 +15,10 @@
 // kernels.  3D levels with width a multiple of 8 run as one fused pass
 // (x/y in shared memory, z from a register ring while marching through z);
 // other 3D levels run as separable 1D passes.
+#include <mutex>
+
 #include "internal.h"
+#include "stencil.cuh"
 #include "tma.cuh"
 
 namespace pat {
@@ -159,6 +162,31 @@ __device__ __forceinline__ float4 f4scale(float w, const float4& v) {
   return make_float4(w * v.x, w * v.y, w * v.z, w * v.w);
 }
 
+// Four consecutive values as two packed FP32x2 pairs (FFMA2 / FMUL2: one
+// instruction per pair, each lane rounded as the scalar instruction would).
+struct F4x2 {
+  float2 p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
+  __device__ __forceinline__ static F4x2 ld(const float* s) {
+    const float4 v = *reinterpret_cast<const float4*>(s);
+    F4x2 r;
+    r.p0 = make_float2(v.x, v.y);
+    r.p1 = make_float2(v.z, v.w);
+    return r;
+  }
+  __device__ __forceinline__ void fma(float2 w, const F4x2& v) {
+    p0 = __ffma2_rn(w, v.p0, p0);
+    p1 = __ffma2_rn(w, v.p1, p1);
+  }
+  __device__ __forceinline__ F4x2 scale(float2 w) const {
+    F4x2 r;
+    r.p0 = __fmul2_rn(w, p0);
+    r.p1 = __fmul2_rn(w, p1);
+    return r;
+  }
+  __device__ __forceinline__ float4 f4() const { return make_float4(p0.x, p0.y, p1.x, p1.y); }
+  __device__ __forceinline__ void st(float* d) const { *reinterpret_cast<float4*>(d) = f4(); }
+};
+
 // Analysis: a CTA makes OX x OY coefficients of each band from the input window
 // rows [2 ky0, 2 ky0 + 2 OY + L - 2) x columns [2 kx0, 2 kx0 + 2 OX + HX) (periodic).
 template <int L>
@@ -181,10 +209,18 @@ __global__ void __launch_bounds__(256) dwt2d_analysis_fast_kernel(const float* _
   __shared__ __align__(16) float hi[G::WY][G::OX];
   const int t = threadIdx.x;
   const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
-  for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-    const int r = i / G::NQ, q = i % G::NQ;
-    const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles the wrap
-    cp_async16(&win[r][4 * q], in + (long long)gy * nx + gx);
+  if (2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny) {  // interior window: no wrap
+    const float* src = in + (long long)(2 * ky0) * nx + 2 * kx0;
+    for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+      const int r = i / G::NQ, q = i - r * G::NQ;
+      cp_async16(&win[r][4 * q], src + (long long)r * nx + 4 * q);
+    }
+  } else {
+    for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+      const int r = i / G::NQ, q = i - r * G::NQ;
+      const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles the wrap
+      cp_async16(&win[r][4 * q], in + (long long)gy * nx + gx);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -217,23 +253,25 @@ __global__ void __launch_bounds__(256) dwt2d_analysis_fast_kernel(const float* _
   __syncthreads();
   // along y: 4 consecutive coefficients of one output row per thread
   const int qx = t % (G::OX / 4), ky = t / (G::OX / 4);
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), hh = a, vv = a, dd = a;
+  F4x2 a, hh, vv, dd;  // packed pairs (columns 0-1, 2-3)
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const float4 l = *reinterpret_cast<const float4*>(&lo[2 * ky + j][4 * qx]);
-    const float4 h = *reinterpret_cast<const float4*>(&hi[2 * ky + j][4 * qx]);
-    a = f4fma(f.h[j], l, a);
-    hh = f4fma(f.g[j], l, hh);  // x low, y high
-    vv = f4fma(f.h[j], h, vv);  // x high, y low
-    dd = f4fma(f.g[j], h, dd);
+    const F4x2 l = F4x2::ld(&lo[2 * ky + j][4 * qx]);
+    const F4x2 h = F4x2::ld(&hi[2 * ky + j][4 * qx]);
+    const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
+    a.fma(hj, l);
+    hh.fma(gj, l);  // x low, y high
+    vv.fma(hj, h);  // x high, y low
+    dd.fma(gj, h);
   }
   const int nx2 = nx >> 1, oy = ky0 + ky, ox = kx0 + 4 * qx;
   if (oy < (ny >> 1) && ox < nx2) {  // nx2 % 4 == 0: the four coefficients are all in or all out
     const long long o = (long long)oy * nx2 + ox;
-    *reinterpret_cast<float4*>(A + o) = a;
-    *reinterpret_cast<float4*>(Hb + o) = f4scale(wdet, hh);
-    *reinterpret_cast<float4*>(Vb + o) = f4scale(wdet, vv);
-    *reinterpret_cast<float4*>(Db + o) = f4scale(wdet, dd);
+    const float2 w2 = dup2(wdet);
+    a.st(A + o);
+    hh.scale(w2).st(Hb + o);
+    vv.scale(w2).st(Vb + o);
+    dd.scale(w2).st(Db + o);
   }
 }
 
@@ -265,11 +303,13 @@ __global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* 
   const int t = threadIdx.x;
   const int nx2 = nx >> 1, ny2 = ny >> 1;
   const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
+  const bool interior = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= nx2 && ky0 + G::OY <= ny2;
   for (int i = t; i < 4 * G::WY * G::NQ; i += G::THREADS) {
-    const int b = i / (G::WY * G::NQ), rq = i % (G::WY * G::NQ);
-    const int r = rq / G::NQ, q = rq % G::NQ;
+    const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
+    const int r = rq / G::NQ, q = rq - r * G::NQ;
     // periodic (a coarse level may be shorter than the halo: wrap repeatedly); nx2 % 4 == 0
-    const int ky = pmod(ky0 - G::LH + r, ny2), kx = pmod(kx0 - G::CX + 4 * q, nx2);
+    const int ky = interior ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, ny2);
+    const int kx = interior ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, nx2);
     const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
     cp_async16(&cw[b][r][4 * q], src + (long long)ky * nx2 + kx);
   }
@@ -283,21 +323,26 @@ __global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* 
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
       const int r = 2 * rp + par;
-      float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sg = sa, sv = sa, sd = sa;
+      F4x2 sa, sg, sv, sd;
 #pragma unroll
       for (int jj = 0; jj < L / 2; ++jj) {
         const int j = 2 * jj + par;
         const int k = rp - jj + G::LH;  // (r - j) / 2 + LH
-        sa = f4fma(f.h[j], *reinterpret_cast<const float4*>(&cw[0][k][4 * q]), sa);
-        sg = f4fma(f.g[j], *reinterpret_cast<const float4*>(&cw[1][k][4 * q]), sg);
-        sv = f4fma(f.h[j], *reinterpret_cast<const float4*>(&cw[2][k][4 * q]), sv);
-        sd = f4fma(f.g[j], *reinterpret_cast<const float4*>(&cw[3][k][4 * q]), sd);
+        const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
+        sa.fma(hj, F4x2::ld(&cw[0][k][4 * q]));
+        sg.fma(gj, F4x2::ld(&cw[1][k][4 * q]));
+        sv.fma(hj, F4x2::ld(&cw[2][k][4 * q]));
+        sd.fma(gj, F4x2::ld(&cw[3][k][4 * q]));
       }
       // lo = sum h A + wdet sum g H;  hi = wdet (sum h V + sum g D)
-      *reinterpret_cast<float4*>(&lo[r][4 * q]) = make_float4(fmaf(wdet, sg.x, sa.x), fmaf(wdet, sg.y, sa.y),
-                                                              fmaf(wdet, sg.z, sa.z), fmaf(wdet, sg.w, sa.w));
-      *reinterpret_cast<float4*>(&hi[r][4 * q]) =
-          make_float4(wdet * (sv.x + sd.x), wdet * (sv.y + sd.y), wdet * (sv.z + sd.z), wdet * (sv.w + sd.w));
+      const float2 w2 = dup2(wdet);
+      F4x2 l2, h2;
+      l2.p0 = __ffma2_rn(w2, sg.p0, sa.p0);
+      l2.p1 = __ffma2_rn(w2, sg.p1, sa.p1);
+      h2.p0 = __fmul2_rn(w2, __fadd2_rn(sv.p0, sd.p0));
+      h2.p1 = __fmul2_rn(w2, __fadd2_rn(sv.p1, sd.p1));
+      l2.st(&lo[r][4 * q]);
+      h2.st(&hi[r][4 * q]);
     }
   }
   __syncthreads();
@@ -363,28 +408,47 @@ struct A3F {
   static constexpr int WX = 2 * OX + HX;
   static constexpr int WY = 2 * OY + L - 2;
   static constexpr int NQ = WX / 4;
+  static constexpr int SLAB_BYTES = NSLOT * WY * WX * 4;  // multiple of 16
+  static constexpr int X_BYTES = WY * OX * 4;
+  static constexpr int SMEM = SLAB_BYTES + 2 * X_BYTES + L * THREADS * 16;
 };
 
 template <int L>
 __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
                                                                   const Bands8 out, float wdet, int cz, const Filt f) {
   using G = A3F<L>;
-  __shared__ __align__(16) float slab[G::NSLOT][G::WY][G::WX];
-  __shared__ __align__(16) float xl[G::WY][G::OX];
-  __shared__ __align__(16) float xh[G::WY][G::OX];
+  extern __shared__ __align__(16) unsigned char dsm[];  // G::SMEM bytes (more than the static 48 KB)
+  auto slab = reinterpret_cast<float(*)[G::WY][G::WX]>(dsm);
+  auto xl = reinterpret_cast<float(*)[G::OX]>(dsm + G::SLAB_BYTES);
+  auto xh = reinterpret_cast<float(*)[G::OX]>(dsm + G::SLAB_BYTES + G::X_BYTES);
+  auto ring = reinterpret_cast<float4(*)[G::THREADS]>(dsm + G::SLAB_BYTES + 2 * G::X_BYTES);  // each thread's
+                                                                                             // quarter values of
+                                                                                             // the last L planes
   const int t = threadIdx.x;
   const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
   const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
   const int kz1 = min(kz0 + cz, nz2);
   const int nplanes = 2 * (kz1 - kz0) + L - 2;  // input planes 2 kz0 .. 2 kz1 + L - 3 (periodic)
+  const bool interior_xy = 2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny;
+  const float* col0 = in + (long long)(2 * ky0) * nx + 2 * kx0;
   auto load = [&](int pl) {
     if (pl < nplanes) {
-      const long long zoff = (long long)((2 * kz0 + pl) % nz) * ny;
+      int z = 2 * kz0 + pl;
+      while (z >= nz) z -= nz;
       float* dst = &slab[pl % G::NSLOT][0][0];
-      for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-        const int r = i / G::NQ, q = i % G::NQ;
-        const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;
-        cp_async16(dst + r * G::WX + 4 * q, in + (zoff + gy) * nx + gx);
+      if (interior_xy) {
+        const float* src = col0 + (long long)z * ny * nx;
+        for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+          const int r = i / G::NQ, q = i - r * G::NQ;
+          cp_async16(dst + r * G::WX + 4 * q, src + (long long)r * nx + 4 * q);
+        }
+      } else {
+        const long long zoff = (long long)z * ny;
+        for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+          const int r = i / G::NQ, q = i - r * G::NQ;
+          const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;
+          cp_async16(dst + r * G::WX + 4 * q, in + (zoff + gy) * nx + gx);
+        }
       }
     }
     cp_async_commit();  // one group per plane (possibly empty) keeps the group count uniform
@@ -394,16 +458,22 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
   // this thread's y-pass output: quarter qq (xb = qq & 1, yb = qq >> 1), row ky, columns 4 qx .. 4 qx + 3
   const int qq = t / 64, ky = (t / 8) % 8, qx = t % 8;
   const int xb = qq & 1, yb = qq >> 1;
-  float4 ring[L];  // quarter values of the last L planes, oldest first
+  const float(*src)[G::OX] = xb ? xh : xl;
+  float2 fy[L];  // the y filter of this quarter, packed
 #pragma unroll
-  for (int j = 0; j < L; ++j) ring[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < L; ++j) fy[j] = dup2(yb ? f.g[j] : f.h[j]);
+  const int oy = ky0 + ky, ox = kx0 + 4 * qx;
+  const bool store = oy < ny2 && ox < nx2;
+  float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
+  float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
+  const float2 wlo = dup2(qq == 0 ? 1.f : wdet), whi = dup2(wdet);
   for (int pl = 0; pl < nplanes; ++pl) {
     load(pl + G::NSLOT - 1);
     cp_async_wait_group<G::NSLOT - 1>();  // this thread's copies of plane pl have landed
     __syncthreads();                      // ... and every other thread's
     const float(*w)[G::WX] = slab[pl % G::NSLOT];
     for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {  // along x
-      const int r = i / (G::OX / 4), q = i % (G::OX / 4);
+      const int r = i / (G::OX / 4), q = i - r * (G::OX / 4);
       float v[8 + G::HX];
 #pragma unroll
       for (int c = 0; c < (8 + G::HX) / 4; ++c) {
@@ -428,29 +498,27 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
       *reinterpret_cast<float4*>(&xh[r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
     }
     __syncthreads();
-    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);  // along y
-    const float(*src)[G::OX] = xb ? xh : xl;
+    F4x2 v4;  // along y
 #pragma unroll
-    for (int j = 0; j < L; ++j)
-      v4 = f4fma(yb ? f.g[j] : f.h[j], *reinterpret_cast<const float4*>(&src[2 * ky + j][4 * qx]), v4);
-#pragma unroll
-    for (int j = 0; j < L - 1; ++j) ring[j] = ring[j + 1];
-    ring[L - 1] = v4;
-    if (pl >= L - 1 && ((pl - (L - 1)) & 1) == 0) {  // ring = input planes 2m .. 2m + L - 1: output plane m
+    for (int j = 0; j < L; ++j) v4.fma(fy[j], F4x2::ld(&src[2 * ky + j][4 * qx]));
+    ring[pl % L][t] = v4.f4();  // read back only by this thread
+    if (pl >= L - 1 && ((pl - (L - 1)) & 1) == 0) {  // ring holds input planes 2m .. 2m + L - 1: output plane m
       const int kz = kz0 + ((pl - (L - 1)) >> 1);
-      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+      const int base = pl - (L - 1);  // plane 2m (relative)
+      F4x2 lo, hi;
 #pragma unroll
       for (int j = 0; j < L; ++j) {
-        lo = f4fma(f.h[j], ring[j], lo);
-        hi = f4fma(f.g[j], ring[j], hi);
+        const float4 r4 = ring[(base + j) % L][t];
+        F4x2 rv;
+        rv.p0 = make_float2(r4.x, r4.y);
+        rv.p1 = make_float2(r4.z, r4.w);
+        lo.fma(dup2(f.h[j]), rv);
+        hi.fma(dup2(f.g[j]), rv);
       }
-      const int oy = ky0 + ky, ox = kx0 + 4 * qx;
-      if (oy < ny2 && ox < nx2) {
+      if (store) {
         const long long o = ((long long)kz * ny2 + oy) * nx2 + ox;
-        float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
-        float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
-        *reinterpret_cast<float4*>(plo + o) = qq == 0 ? lo : f4scale(wdet, lo);
-        *reinterpret_cast<float4*>(phi + o) = f4scale(wdet, hi);
+        lo.scale(wlo).st(plo + o);
+        hi.scale(whi).st(phi + o);
       }
     }
   }
@@ -485,13 +553,15 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
   const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
   const int kz1 = min(kz0 + cz, cz2);
   const int nplanes = kz1 - kz0 + G::LH;  // coefficient planes kz0 - LH .. kz1 - 1 (periodic)
+  const bool interior_xy = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= cx && ky0 + G::OY <= cy;
   auto load = [&](int pl) {
     if (pl < nplanes) {
       const long long zoff = (long long)pmod(kz0 - G::LH + pl, cz2) * cy;
       for (int i = t; i < 8 * G::WY * G::NQ; i += G::THREADS) {
-        const int b = i / (G::WY * G::NQ), rq = i % (G::WY * G::NQ);
-        const int r = rq / G::NQ, q = rq % G::NQ;
-        const int ky = pmod(ky0 - G::LH + r, cy), kx = pmod(kx0 - G::CX + 4 * q, cx);
+        const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
+        const int r = rq / G::NQ, q = rq - r * G::NQ;
+        const int ky = interior_xy ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, cy);
+        const int kx = interior_xy ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, cx);
         cp_async16(&cw[pl % G::NSLOT][b][r][4 * q], band_sel(in, b) + (zoff + ky) * cx + kx);
       }
     }
@@ -515,24 +585,27 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
       const int c0 = zb << 2;
 #pragma unroll
       for (int par = 0; par < 2; ++par) {
-        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;  // codes c0 | 0, 1, 2, 3
+        F4x2 s0, s1, s2, s3;  // codes c0 | 0, 1, 2, 3
 #pragma unroll
         for (int jj = 0; jj < L / 2; ++jj) {
           const int j = 2 * jj + par;
           const int k = rp - jj + G::LH;
-          s0 = f4fma(f.h[j], *reinterpret_cast<const float4*>(&W[c0 | 0][k][4 * q]), s0);
-          s2 = f4fma(f.g[j], *reinterpret_cast<const float4*>(&W[c0 | 2][k][4 * q]), s2);
-          s1 = f4fma(f.h[j], *reinterpret_cast<const float4*>(&W[c0 | 1][k][4 * q]), s1);
-          s3 = f4fma(f.g[j], *reinterpret_cast<const float4*>(&W[c0 | 3][k][4 * q]), s3);
+          const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
+          s0.fma(hj, F4x2::ld(&W[c0 | 0][k][4 * q]));
+          s2.fma(gj, F4x2::ld(&W[c0 | 2][k][4 * q]));
+          s1.fma(hj, F4x2::ld(&W[c0 | 1][k][4 * q]));
+          s3.fma(gj, F4x2::ld(&W[c0 | 3][k][4 * q]));
         }
         const int r = 2 * rp + par;
         // x-low rows: code c0 (weight 1 only for the approximation) + code c0|2; x-high rows: codes c0|1, c0|3
-        const float w0 = zb ? wdet : 1.f;
-        *reinterpret_cast<float4*>(&yl[zb][r][4 * q]) =
-            make_float4(fmaf(wdet, s2.x, w0 * s0.x), fmaf(wdet, s2.y, w0 * s0.y), fmaf(wdet, s2.z, w0 * s0.z),
-                        fmaf(wdet, s2.w, w0 * s0.w));
-        *reinterpret_cast<float4*>(&yh[zb][r][4 * q]) =
-            make_float4(wdet * (s1.x + s3.x), wdet * (s1.y + s3.y), wdet * (s1.z + s3.z), wdet * (s1.w + s3.w));
+        const float2 w0 = dup2(zb ? wdet : 1.f), w2 = dup2(wdet);
+        F4x2 l2, h2;
+        l2.p0 = __ffma2_rn(w2, s2.p0, __fmul2_rn(w0, s0.p0));
+        l2.p1 = __ffma2_rn(w2, s2.p1, __fmul2_rn(w0, s0.p1));
+        h2.p0 = __fmul2_rn(w2, __fadd2_rn(s1.p0, s3.p0));
+        h2.p1 = __fmul2_rn(w2, __fadd2_rn(s1.p1, s3.p1));
+        l2.st(&yl[zb][r][4 * q]);
+        h2.st(&yh[zb][r][4 * q]);
       }
     }
     __syncthreads();
@@ -575,18 +648,36 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
       const int iy = 2 * ky0 + pr, ix = 2 * kx0 + 4 * pq;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        F4x2 v;
 #pragma unroll
         for (int jj = 0; jj < L / 2; ++jj) {
           const int j = 2 * jj + e;
-          v = f4fma(f.h[j], rlo[L / 2 - 1 - jj], v);
-          v = f4fma(f.g[j], rhi[L / 2 - 1 - jj], v);
+          F4x2 a, b;
+          a.p0 = make_float2(rlo[L / 2 - 1 - jj].x, rlo[L / 2 - 1 - jj].y);
+          a.p1 = make_float2(rlo[L / 2 - 1 - jj].z, rlo[L / 2 - 1 - jj].w);
+          b.p0 = make_float2(rhi[L / 2 - 1 - jj].x, rhi[L / 2 - 1 - jj].y);
+          b.p1 = make_float2(rhi[L / 2 - 1 - jj].z, rhi[L / 2 - 1 - jj].w);
+          v.fma(dup2(f.h[j]), a);
+          v.fma(dup2(f.g[j]), b);
         }
-        if (iy < ny && ix < nx)
-          *reinterpret_cast<float4*>(out + ((long long)(2 * m + e) * ny + iy) * nx + ix) = v;
+        if (iy < ny && ix < nx) v.st(out + ((long long)(2 * m + e) * ny + iy) * nx + ix);
       }
     }
   }
+}
+
+template <int L>
+cudaError_t launch_a3(dim3 grid, cudaStream_t st, const float* in, int nx, int ny, int nz, const Bands8& b, float wdet,
+                      int cz, const Filt& f) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(dwt3d_analysis_fast_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                A3F<L>::SMEM);
+  });
+  if (attr != cudaSuccess) return attr;
+  dwt3d_analysis_fast_kernel<L><<<grid, A3F<L>::THREADS, A3F<L>::SMEM, st>>>(in, nx, ny, nz, b, wdet, cz, f);
+  return cudaGetLastError();
 }
 
 // z planes per CTA for a level with coefficient-column count `cols` and
@@ -750,10 +841,9 @@ cudaError_t dwt3d_analysis_level(const float* in, int nx, int ny, int nz, float*
   const long long cols = (long long)((nx2 + 31) / 32) * ((ny2 + 7) / 8);
   const int cz = chunk3d(cols, nz2);
   dim3 grid((nx2 + 31) / 32, (ny2 + 7) / 8, (nz2 + cz - 1) / cz);
-  if (L == 2) dwt3d_analysis_fast_kernel<2><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
-  if (L == 4) dwt3d_analysis_fast_kernel<4><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
-  if (L == 8) dwt3d_analysis_fast_kernel<8><<<grid, 256, 0, st>>>(in, nx, ny, nz, b, wdet, cz, f);
-  return cudaGetLastError();
+  if (L == 2) return launch_a3<2>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
+  if (L == 4) return launch_a3<4>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
+  return launch_a3<8>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
 }
 
 cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int nx, int ny, int nz, float* out,

@@ -140,6 +140,67 @@ __device__ __forceinline__ void lap_2x4_x2(const float* __restrict__ S, int pitc
   }
 }
 
+// Packed pair term: (a + b) - 2c as fma(c, -2, a + b), or the difference form
+// (a - c) + (b - c) with -c formed exactly; either equals its scalar form bit
+// for bit in each lane.
+template <bool DIFF>
+__device__ __forceinline__ float2 pair_term2(float2 a, float2 b, float2 c, float2 nc) {
+  return DIFF ? __fadd2_rn(__fadd2_rn(a, nc), __fadd2_rn(b, nc)) : __ffma2_rn(c, dup2(-2.f), __fadd2_rn(a, b));
+}
+
+// lap_2x4<R, DIFF, ACC> in packed FP32x2 arithmetic: same operand order and
+// rounding (y taps, then x taps), L[rr][j] as scalars for the callers.
+template <int R, bool DIFF = false, bool ACC = false>
+__device__ __forceinline__ void lap_2x4_p(const float* __restrict__ S, int pitch, int srow, int scol,
+                                          const float2 (&w2)[R + 1], float L[2][4]) {
+  float4 col[2 + 2 * R];
+#pragma unroll
+  for (int i = 0; i < 2 + 2 * R; ++i) col[i] = *reinterpret_cast<const float4*>(S + (srow - R + i) * pitch + scol);
+  float2 A[2][2];
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 c = p ? hi2(col[rr + R]) : lo2(col[rr + R]);
+      const float2 nc = __fmul2_rn(c, dup2(-1.f));
+      float2 acc = ACC ? make_float2(L[rr][2 * p], L[rr][2 * p + 1]) : dup2(0.f);
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float2 a = p ? hi2(col[rr + R + m]) : lo2(col[rr + R + m]);
+        const float2 b = p ? hi2(col[rr + R - m]) : lo2(col[rr + R - m]);
+        acc = __ffma2_rn(w2[m], pair_term2<DIFF>(a, b, c, nc), acc);
+      }
+      A[rr][p] = acc;
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    float f[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(S + (srow + rr) * pitch + scol - 8 + 4 * q);
+      f[4 * q + 0] = v.x;
+      f[4 * q + 1] = v.y;
+      f[4 * q + 2] = v.z;
+      f[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 c = make_float2(f[8 + 2 * p], f[9 + 2 * p]);
+      const float2 nc = __fmul2_rn(c, dup2(-1.f));
+      float2 acc = A[rr][p];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float2 a = make_float2(f[8 + 2 * p + m], f[9 + 2 * p + m]);
+        const float2 b = make_float2(f[8 + 2 * p - m], f[9 + 2 * p - m]);
+        acc = __ffma2_rn(w2[m], pair_term2<DIFF>(a, b, c, nc), acc);
+      }
+      L[rr][2 * p] = acc.x;
+      L[rr][2 * p + 1] = acc.y;
+    }
+  }
+}
+
 // 16-byte load of data read once per launch (streamed: no L1 allocation)
 __device__ __forceinline__ float4 ld_stream4(const float* p) {
   float4 v;

