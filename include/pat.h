@@ -220,12 +220,14 @@ pat_status pat_solve_batched(pat_plan* const* plans, int B, const float* const* 
  * CG (Sec. 4) is run for many independent problems at once.
  *
  * pat_batch_create — group B plans into one batch.  Every plan must be 2D,
- * with a constant speed of sound, the same stencil order and nx % 4 == 0, and
+ * with the same stencil order, nx % 4 == 0 and no absorbing layer, and
  * appear once (the batch uses each plan's device buffers; the plans must
  * outlive the batch and must not be used concurrently with it).  Grid size,
- * time samples, sensors, wavelet, alpha and s may differ.  All instances'
- * 64-column tiles form one table; each time step of K or K* is one launch
- * over the tiles of the instances still running.  The tile height (64 or 32
+ * time samples, sensors, medium (constant or varying speed of sound),
+ * wavelet, alpha and s may differ.  All instances' 64-column tiles form one
+ * table; each time step of K or K* walks the tiles of the instances still
+ * running (one launch per step, or all steps in one launch: see
+ * pat_batch_launch).  The tile height (64 or 32
  * rows) is chosen by timing both on the first steps of a batched K and K*
  * (an autotuner; PAT_BATCH_TILE_Y=64|32 in the environment fixes it).  The
  * batched K* keeps its state Z = kappa Q as a compensated pair in the plans'

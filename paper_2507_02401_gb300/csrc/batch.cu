@@ -49,7 +49,6 @@ bool device_ptr(const void* p) {
 // Why a plan cannot join a batch, or nullptr.
 const char* ineligible(const pat_plan* p, int R) {
   if (p->dim != 2) return "batched instances are 2D";
-  if (p->varc) return "batched instances have a constant medium";
   if (p->R != R) return "batched instances share one stencil order";
   if (p->n[0] % 4 != 0) return "batched instances have nx divisible by 4";
   if (p->sponge_w > 0) return "batched instances have no absorbing layer";
@@ -82,6 +81,8 @@ pat_status build_tables(pat_batch* b, int variant, cudaStream_t st) {
     I.corners = p->corners;
     I.kappa0 = p->kappa0;
     I.kappa0_lo = p->kappa0_lo;
+    I.kappa = p->varc ? p->d_kappa : nullptr;
+    I.kappa_lo = p->varc ? p->d_kappa_lo : nullptr;
     I.img = p->d_img;
     I.P[0] = p->d_wv[0];
     I.P[1] = p->d_wv[1];

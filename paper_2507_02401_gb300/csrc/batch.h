@@ -1,5 +1,5 @@
-// Batched 2D engine: many independent constant-medium problems advanced one
-// time step per launch over a common table of 64-column tiles.
+// Batched 2D engine: many independent problems (constant or varying medium)
+// advanced one time step per launch over a common table of 64-column tiles.
 #pragma once
 
 #include <vector>
@@ -14,6 +14,8 @@ struct BInst {
   int tile0;  // first entry of this instance in the tile table
   int ns, corners;
   float kappa0, kappa0_lo;
+  const float* kappa;     // per-cell kappa of a varying medium, or nullptr (constant kappa0 + kappa0_lo)
+  const float* kappa_lo;  // its rounding residual (forward), or nullptr
   const float* img;  // forward input P^0 / adjoint output x (the plan's image buffer)
   float* P[2];       // ping-pong fields: P^n (forward) or Z^m = kappa Q^m (adjoint)
   float* P_lo[2];    // adjoint: ping-pong compensation Z_lo^m

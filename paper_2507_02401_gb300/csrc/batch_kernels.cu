@@ -1,6 +1,7 @@
 // Batched 2D step kernel: one launch advances every running instance of a
 // batch by one time step of the increment form (paper Sec. 2, Eq.
-// wave_equation, eliminated to p only; constant medium):
+// wave_equation, eliminated to p only; constant or varying medium, kappa
+// per cell read with the row when the instance has a varying medium):
 //
 //   forward, n = t:          D <- D + c_lap kappa L P^n,   P^{n+1} = P^n + D,   y[., n] = S P^n
 //   adjoint, m = nt - 1 - t: G <- G + S^T r_m + c_lap L Z^{m+1},  Z^m = Z^{m+1} + kappa G
@@ -89,6 +90,9 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
 
   const int t = threadIdx.x;
   const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * RUN;
+  float2 w2[R + 1];  // stencil weights, packed
+#pragma unroll
+  for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
 
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -199,6 +203,7 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
       const float* PL = P + G::PBOX;           // adjoint: Z_lo
       const float c_lap = (n == 0 || final_step) ? 0.5f : 1.f;
       const float ckh = c_lap * I.kappa0, ckl = c_lap * I.kappa0_lo;
+      const bool varying = I.kappa != nullptr;  // uniform over the tile (one instance)
       float lo[RUN][4];  // adjoint: the Z_lo part of the stencil, first pass
       if (ADJ) stencil_run<R, RUN, BW, XH>(PL, r0, c0, a.w, lo);
       float4 win[2 * R + 1];
@@ -212,26 +217,39 @@ __global__ void __launch_bounds__(GB<R, TY, ADJ>::THREADS) batch_step_kernel(con
         load_row20(P + brow * BW + c0, f);
         float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ADJ) zl4 = *reinterpret_cast<const float4*>(PL + brow * BW + XH + c0);
+        // a varying medium's kappa (forward: hi and lo parts) for this row, in flight during the stencil
+        const int gy = gy0 + r0 + rr;
+        const bool own = gy < ny && gx < nx;
+        float4 kh = make_float4(0.f, 0.f, 0.f, 0.f), kl = kh;
+        if (varying && own) {
+          kh = __ldg(reinterpret_cast<const float4*>(I.kappa + (long long)gy * nx + gx));
+          if (!ADJ) kl = __ldg(reinterpret_cast<const float4*>(I.kappa_lo + (long long)gy * nx + gx));
+        }
         float dn[4], pn[4], pl[4];
+        float st4[4];
+        stencil_cells2<R, ADJ>(win, f, w2, st4);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float c = f[8 + j];
-          if (!ADJ) {  // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
-            const float acc = stencil_cell<R, false>(win, f, j, a.w);
-            dn[j] = f4get(d4[rr], j) + fmaf(ckh, acc, ckl * acc);
+          if (!ADJ) {  // zero-sum pair form (a + b) - 2c per tap
+            const float acc = st4[j];
+            // D += c_lap (kappa_hi + kappa_lo) L, the product rounded once before it meets D
+            const float inc = varying ? fmaf(c_lap * f4get(kh, j), acc, (c_lap * f4get(kl, j)) * acc)
+                                      : fmaf(ckh, acc, ckl * acc);
+            dn[j] = f4get(d4[rr], j) + inc;
             pn[j] = c + dn[j];
             pl[j] = 0.f;
           } else {
-            const float acc = stencil_cell<R, true>(win, f, j, a.w) + lo[rr][j];
+            const float acc = st4[j] + lo[rr][j];  // difference form on Z
             const float g = fmaf(c_lap, acc, f4get(d4[rr], j));
             dn[j] = g;
             float e = 0.f;
-            pn[j] = final_step ? g : two_sum(c, fmaf(I.kappa0, g, I.kappa0_lo * g), e);  // Z += kappa G
+            const float u = varying ? f4get(kh, j) * g : fmaf(I.kappa0, g, I.kappa0_lo * g);  // kappa G
+            pn[j] = final_step ? g : two_sum(c, u, e);                                          // Z += kappa G
             pl[j] = f4get(zl4, j) + e;
           }
         }
-        const int gy = gy0 + r0 + rr;
-        if (gy < ny && gx < nx) {
+        if (own) {
           const long long gi = (long long)gy * nx + gx;
           *reinterpret_cast<float4*>(out + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
           if (!final_step) {

@@ -154,6 +154,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ float4 f4fma(float w, const float4& v, const float4& a) {
   return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
@@ -187,8 +190,17 @@ struct F4x2 {
   __device__ __forceinline__ void st(float* d) const { *reinterpret_cast<float4*>(d) = f4(); }
 };
 
-// Analysis: a CTA makes OX x OY coefficients of each band from the input window
-// rows [2 ky0, 2 ky0 + 2 OY + L - 2) x columns [2 kx0, 2 kx0 + 2 OX + HX) (periodic).
+// Programmatic dependent launch: a level's grid may start while the previous
+// level's grid drains; griddepcontrol.wait (before any read of the previous
+// level's output) blocks until that grid has completed and its writes are
+// visible.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Analysis: tile (kx0, ky0) gives OX x OY coefficients of each band from the
+// input window rows [2 ky0, 2 ky0 + 2 OY + L - 2) x columns [2 kx0, 2 kx0 +
+// 2 OX + HX) (periodic).  Persistent CTAs walk the tiles, staging the next
+// tile's window (cp.async, second buffer) while filtering the current one.
 template <int L>
 struct A2F {
   static constexpr int OX = 64, OY = 16, THREADS = 256;
@@ -196,88 +208,108 @@ struct A2F {
   static constexpr int WX = 2 * OX + HX;
   static constexpr int WY = 2 * OY + L - 2;
   static constexpr int NQ = WX / 4;
+  static constexpr int WIN = WY * WX;  // floats per window buffer (multiple of 4)
+  static constexpr int LOHI = WY * OX;
+  static constexpr int SMEM = (2 * WIN + 2 * LOHI) * 4;
 };
 
 template <int L>
 __global__ void __launch_bounds__(256) dwt2d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny,
                                                                   float* __restrict__ A, float* __restrict__ Hb,
                                                                   float* __restrict__ Vb, float* __restrict__ Db,
-                                                                  float wdet, const Filt f) {
+                                                                  float wdet, const Filt f, int tiles_x,
+                                                                  int ntiles) {
   using G = A2F<L>;
-  __shared__ __align__(16) float win[G::WY][G::WX];
-  __shared__ __align__(16) float lo[G::WY][G::OX];
-  __shared__ __align__(16) float hi[G::WY][G::OX];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float* win0 = reinterpret_cast<float*>(dsm);          // two window buffers
+  auto lo = reinterpret_cast<float(*)[G::OX]>(win0 + 2 * G::WIN);
+  auto hi = reinterpret_cast<float(*)[G::OX]>(win0 + 2 * G::WIN + G::LOHI);
   const int t = threadIdx.x;
-  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
-  if (2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny) {  // interior window: no wrap
-    const float* src = in + (long long)(2 * ky0) * nx + 2 * kx0;
-    for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-      const int r = i / G::NQ, q = i - r * G::NQ;
-      cp_async16(&win[r][4 * q], src + (long long)r * nx + 4 * q);
-    }
-  } else {
-    for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-      const int r = i / G::NQ, q = i - r * G::NQ;
-      const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles the wrap
-      cp_async16(&win[r][4 * q], in + (long long)gy * nx + gx);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // along x: outputs 4q .. 4q+3 of window row r read window columns 8q .. 8q + 6 + L - 1
-  for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {
-    const int r = i / (G::OX / 4), q = i % (G::OX / 4);
-    float v[8 + G::HX];
-#pragma unroll
-    for (int c = 0; c < (8 + G::HX) / 4; ++c) {
-      const float4 w4 = *reinterpret_cast<const float4*>(&win[r][8 * q + 4 * c]);
-      v[4 * c] = w4.x;
-      v[4 * c + 1] = w4.y;
-      v[4 * c + 2] = w4.z;
-      v[4 * c + 3] = w4.w;
-    }
-    float sl[4], sh[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      sl[k] = 0.f;
-      sh[k] = 0.f;
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        sl[k] = fmaf(f.h[j], v[2 * k + j], sl[k]);
-        sh[k] = fmaf(f.g[j], v[2 * k + j], sh[k]);
+  griddep_wait();
+  griddep_trigger();
+  auto stage = [&](int tile, float* w) {
+    const int kx0 = (tile % tiles_x) * G::OX, ky0 = (tile / tiles_x) * G::OY;
+    if (2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny) {  // interior window: no wrap
+      const float* src = in + (long long)(2 * ky0) * nx + 2 * kx0;
+      for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+        const int r = i / G::NQ, q = i - r * G::NQ;
+        cp_async16(w + r * G::WX + 4 * q, src + (long long)r * nx + 4 * q);
+      }
+    } else {
+      for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
+        const int r = i / G::NQ, q = i - r * G::NQ;
+        const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles
+        cp_async16(w + r * G::WX + 4 * q, in + (long long)gy * nx + gx);  // the wrap
       }
     }
-    *reinterpret_cast<float4*>(&lo[r][4 * q]) = make_float4(sl[0], sl[1], sl[2], sl[3]);
-    *reinterpret_cast<float4*>(&hi[r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
-  }
-  __syncthreads();
-  // along y: 4 consecutive coefficients of one output row per thread
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage(tile, win0);
+  cp_async_commit();
   const int qx = t % (G::OX / 4), ky = t / (G::OX / 4);
-  F4x2 a, hh, vv, dd;  // packed pairs (columns 0-1, 2-3)
+  const int nx2 = nx >> 1, ny2 = ny >> 1;
+  const float2 w2 = dup2(wdet);
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage(nxt, win0 + ((k + 1) & 1) * G::WIN);  // read two barriers ago: free
+    cp_async_commit();
+    cp_async_wait_group<1>();  // this tile's window has landed (this thread's copies)
+    __syncthreads();           // ... and every thread's
+    const float(*win)[G::WX] = reinterpret_cast<const float(*)[G::WX]>(win0 + (k & 1) * G::WIN);
+    // along x: outputs 4q .. 4q+3 of window row r read window columns 8q .. 8q + 6 + L - 1
+    for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {
+      const int r = i / (G::OX / 4), q = i % (G::OX / 4);
+      float v[8 + G::HX];
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    const F4x2 l = F4x2::ld(&lo[2 * ky + j][4 * qx]);
-    const F4x2 h = F4x2::ld(&hi[2 * ky + j][4 * qx]);
-    const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
-    a.fma(hj, l);
-    hh.fma(gj, l);  // x low, y high
-    vv.fma(hj, h);  // x high, y low
-    dd.fma(gj, h);
-  }
-  const int nx2 = nx >> 1, oy = ky0 + ky, ox = kx0 + 4 * qx;
-  if (oy < (ny >> 1) && ox < nx2) {  // nx2 % 4 == 0: the four coefficients are all in or all out
-    const long long o = (long long)oy * nx2 + ox;
-    const float2 w2 = dup2(wdet);
-    a.st(A + o);
-    hh.scale(w2).st(Hb + o);
-    vv.scale(w2).st(Vb + o);
-    dd.scale(w2).st(Db + o);
+      for (int c = 0; c < (8 + G::HX) / 4; ++c) {
+        const float4 w4 = *reinterpret_cast<const float4*>(&win[r][8 * q + 4 * c]);
+        v[4 * c] = w4.x;
+        v[4 * c + 1] = w4.y;
+        v[4 * c + 2] = w4.z;
+        v[4 * c + 3] = w4.w;
+      }
+      float sl[4], sh[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        sl[kk] = 0.f;
+        sh[kk] = 0.f;
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+          sl[kk] = fmaf(f.h[j], v[2 * kk + j], sl[kk]);
+          sh[kk] = fmaf(f.g[j], v[2 * kk + j], sh[kk]);
+        }
+      }
+      *reinterpret_cast<float4*>(&lo[r][4 * q]) = make_float4(sl[0], sl[1], sl[2], sl[3]);
+      *reinterpret_cast<float4*>(&hi[r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+    }
+    __syncthreads();
+    // along y: 4 consecutive coefficients of one output row per thread
+    F4x2 a, hh, vv, dd;  // packed pairs (columns 0-1, 2-3)
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      const F4x2 l = F4x2::ld(&lo[2 * ky + j][4 * qx]);
+      const F4x2 h = F4x2::ld(&hi[2 * ky + j][4 * qx]);
+      const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
+      a.fma(hj, l);
+      hh.fma(gj, l);  // x low, y high
+      vv.fma(hj, h);  // x high, y low
+      dd.fma(gj, h);
+    }
+    const int oy = (tile / tiles_x) * G::OY + ky, ox = (tile % tiles_x) * G::OX + 4 * qx;
+    if (oy < ny2 && ox < nx2) {  // nx2 % 4 == 0: the four coefficients are all in or all out
+      const long long o = (long long)oy * nx2 + ox;
+      a.st(A + o);
+      hh.scale(w2).st(Hb + o);
+      vv.scale(w2).st(Vb + o);
+      dd.scale(w2).st(Db + o);
+    }
   }
 }
 
-// Synthesis: a CTA makes the 2 OX x 2 OY pixels of coefficient block
+// Synthesis: tile (kx0, ky0) gives the 2 OX x 2 OY pixels of coefficient block
 // (kx0 .. kx0+OX-1, ky0 .. ky0+OY-1) from the coefficient window rows
-// [ky0 - LH, ky0 + OY) x columns [kx0 - CX, kx0 + OX) of each band (periodic).
+// [ky0 - LH, ky0 + OY) x columns [kx0 - CX, kx0 + OX) of each band
+// (periodic); persistent CTAs, next window staged while filtering.
 template <int L>
 struct S2F {
   static constexpr int OX = 64, OY = 16, THREADS = 256;
@@ -288,6 +320,9 @@ struct S2F {
   static constexpr int NQ = WX / 4;
   static constexpr int K0 = (CX - LH) & ~1;        // first (even) window column a pixel quad reads
   static constexpr int NK2 = (CX + 2 - K0) / 2;    // float2 loads per pixel quad
+  static constexpr int WIN = 4 * WY * WX;          // floats per window buffer (four bands)
+  static constexpr int LOHI = 2 * OY * WX;
+  static constexpr int SMEM = (2 * WIN + 2 * LOHI) * 4;
 };
 
 template <int L>
@@ -295,85 +330,169 @@ __global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* 
                                                                    const float* __restrict__ Hb,
                                                                    const float* __restrict__ Vb,
                                                                    const float* __restrict__ Db, float wdet, int nx,
-                                                                   int ny, float* __restrict__ out, const Filt f) {
+                                                                   int ny, float* __restrict__ out, const Filt f,
+                                                                   int tiles_x, int ntiles) {
   using G = S2F<L>;
-  __shared__ __align__(16) float cw[4][G::WY][G::WX];
-  __shared__ __align__(16) float lo[2 * G::OY][G::WX];
-  __shared__ __align__(16) float hi[2 * G::OY][G::WX];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float* cw0 = reinterpret_cast<float*>(dsm);  // two window buffers [4][WY][WX]
+  auto lo = reinterpret_cast<float(*)[G::WX]>(cw0 + 2 * G::WIN);
+  auto hi = reinterpret_cast<float(*)[G::WX]>(cw0 + 2 * G::WIN + G::LOHI);
   const int t = threadIdx.x;
   const int nx2 = nx >> 1, ny2 = ny >> 1;
-  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY;
-  const bool interior = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= nx2 && ky0 + G::OY <= ny2;
-  for (int i = t; i < 4 * G::WY * G::NQ; i += G::THREADS) {
-    const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
-    const int r = rq / G::NQ, q = rq - r * G::NQ;
-    // periodic (a coarse level may be shorter than the halo: wrap repeatedly); nx2 % 4 == 0
-    const int ky = interior ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, ny2);
-    const int kx = interior ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, nx2);
-    const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
-    cp_async16(&cw[b][r][4 * q], src + (long long)ky * nx2 + kx);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // along y: pixel row r of the block (row 2 ky0 + r) at every window column;
-  // x[2k + j] gets h_j a_k + g_j d_k, so row r reads window rows (r - j)/2 + LH, j = r mod 2, r mod 2 + 2, ...
-  // (each item is a row pair, so the filter taps of both parities are compile-time indices)
-  for (int i = t; i < G::OY * G::NQ; i += G::THREADS) {
-    const int rp = i / G::NQ, q = i % G::NQ;
-#pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      const int r = 2 * rp + par;
-      F4x2 sa, sg, sv, sd;
-#pragma unroll
-      for (int jj = 0; jj < L / 2; ++jj) {
-        const int j = 2 * jj + par;
-        const int k = rp - jj + G::LH;  // (r - j) / 2 + LH
-        const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
-        sa.fma(hj, F4x2::ld(&cw[0][k][4 * q]));
-        sg.fma(gj, F4x2::ld(&cw[1][k][4 * q]));
-        sv.fma(hj, F4x2::ld(&cw[2][k][4 * q]));
-        sd.fma(gj, F4x2::ld(&cw[3][k][4 * q]));
-      }
-      // lo = sum h A + wdet sum g H;  hi = wdet (sum h V + sum g D)
-      const float2 w2 = dup2(wdet);
-      F4x2 l2, h2;
-      l2.p0 = __ffma2_rn(w2, sg.p0, sa.p0);
-      l2.p1 = __ffma2_rn(w2, sg.p1, sa.p1);
-      h2.p0 = __fmul2_rn(w2, __fadd2_rn(sv.p0, sd.p0));
-      h2.p1 = __fmul2_rn(w2, __fadd2_rn(sv.p1, sd.p1));
-      l2.st(&lo[r][4 * q]);
-      h2.st(&hi[r][4 * q]);
+  griddep_wait();
+  griddep_trigger();
+  auto stage = [&](int tile, float* w) {
+    const int kx0 = (tile % tiles_x) * G::OX, ky0 = (tile / tiles_x) * G::OY;
+    const bool interior = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= nx2 && ky0 + G::OY <= ny2;
+    for (int i = t; i < 4 * G::WY * G::NQ; i += G::THREADS) {
+      const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
+      const int r = rq / G::NQ, q = rq - r * G::NQ;
+      // periodic (a coarse level may be shorter than the halo: wrap repeatedly); nx2 % 4 == 0
+      const int ky = interior ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, ny2);
+      const int kx = interior ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, nx2);
+      const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
+      cp_async16(w + (b * G::WY + r) * G::WX + 4 * q, src + (long long)ky * nx2 + kx);
     }
-  }
-  __syncthreads();
-  // along x: pixels 4p .. 4p+3 of row r; pixel i reads window columns (i - j)/2 + CX
-  for (int i = t; i < 2 * G::OY * (2 * G::OX / 4); i += G::THREADS) {
-    const int r = i / (2 * G::OX / 4), p = i % (2 * G::OX / 4);
-    float l[2 * G::NK2], h[2 * G::NK2];  // window columns 2p + K0 ..
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage(tile, cw0);
+  cp_async_commit();
+  const float2 w2 = dup2(wdet);
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage(nxt, cw0 + ((k + 1) & 1) * G::WIN);
+    cp_async_commit();
+    cp_async_wait_group<1>();
+    __syncthreads();
+    const float(*cw)[G::WY][G::WX] = reinterpret_cast<const float(*)[G::WY][G::WX]>(cw0 + (k & 1) * G::WIN);
+    // along y: pixel row r of the block at every window column; x[2k + j] gets h_j a_k + g_j d_k, so
+    // row r reads window rows (r - j)/2 + LH, j = r mod 2, r mod 2 + 2, ... (each item is a row pair,
+    // so the filter taps of both parities are compile-time indices)
+    for (int i = t; i < G::OY * G::NQ; i += G::THREADS) {
+      const int rp = i / G::NQ, q = i % G::NQ;
 #pragma unroll
-    for (int c = 0; c < G::NK2; ++c) {
-      const float2 l2 = *reinterpret_cast<const float2*>(&lo[r][2 * p + G::K0 + 2 * c]);
-      const float2 h2 = *reinterpret_cast<const float2*>(&hi[r][2 * p + G::K0 + 2 * c]);
-      l[2 * c] = l2.x;
-      l[2 * c + 1] = l2.y;
-      h[2 * c] = h2.x;
-      h[2 * c + 1] = h2.y;
-    }
-    float v[4];
+      for (int par = 0; par < 2; ++par) {
+        const int r = 2 * rp + par;
+        F4x2 sa, sg, sv, sd;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      v[e] = 0.f;
-#pragma unroll
-      for (int jj = 0; jj < L / 2; ++jj) {
-        const int j = 2 * jj + (e & 1);
-        const int k = ((e - j) >> 1) + G::CX - G::K0;  // index into l/h (window column - 2p - K0)
-        v[e] = fmaf(f.h[j], l[k], v[e]);
-        v[e] = fmaf(f.g[j], h[k], v[e]);
+        for (int jj = 0; jj < L / 2; ++jj) {
+          const int j = 2 * jj + par;
+          const int kr = rp - jj + G::LH;  // (r - j) / 2 + LH
+          const float2 hj = dup2(f.h[j]), gj = dup2(f.g[j]);
+          sa.fma(hj, F4x2::ld(&cw[0][kr][4 * q]));
+          sg.fma(gj, F4x2::ld(&cw[1][kr][4 * q]));
+          sv.fma(hj, F4x2::ld(&cw[2][kr][4 * q]));
+          sd.fma(gj, F4x2::ld(&cw[3][kr][4 * q]));
+        }
+        // lo = sum h A + wdet sum g H;  hi = wdet (sum h V + sum g D)
+        F4x2 l2, h2;
+        l2.p0 = __ffma2_rn(w2, sg.p0, sa.p0);
+        l2.p1 = __ffma2_rn(w2, sg.p1, sa.p1);
+        h2.p0 = __fmul2_rn(w2, __fadd2_rn(sv.p0, sd.p0));
+        h2.p1 = __fmul2_rn(w2, __fadd2_rn(sv.p1, sd.p1));
+        l2.st(&lo[r][4 * q]);
+        h2.st(&hi[r][4 * q]);
       }
     }
-    const int iy = 2 * ky0 + r, ix = 2 * kx0 + 4 * p;
-    if (iy < ny && ix < nx) *reinterpret_cast<float4*>(out + (long long)iy * nx + ix) = make_float4(v[0], v[1], v[2], v[3]);
+    __syncthreads();
+    // along x: pixels 4p .. 4p+3 of row r; pixel i reads window columns (i - j)/2 + CX
+    const int ky0 = (tile / tiles_x) * G::OY, kx0 = (tile % tiles_x) * G::OX;
+    for (int i = t; i < 2 * G::OY * (2 * G::OX / 4); i += G::THREADS) {
+      const int r = i / (2 * G::OX / 4), p = i % (2 * G::OX / 4);
+      float l[2 * G::NK2], h[2 * G::NK2];  // window columns 2p + K0 ..
+#pragma unroll
+      for (int c = 0; c < G::NK2; ++c) {
+        const float2 l2 = *reinterpret_cast<const float2*>(&lo[r][2 * p + G::K0 + 2 * c]);
+        const float2 h2 = *reinterpret_cast<const float2*>(&hi[r][2 * p + G::K0 + 2 * c]);
+        l[2 * c] = l2.x;
+        l[2 * c + 1] = l2.y;
+        h[2 * c] = h2.x;
+        h[2 * c + 1] = h2.y;
+      }
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[e] = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < L / 2; ++jj) {
+          const int j = 2 * jj + (e & 1);
+          const int kk = ((e - j) >> 1) + G::CX - G::K0;  // index into l/h (window column - 2p - K0)
+          v[e] = fmaf(f.h[j], l[kk], v[e]);
+          v[e] = fmaf(f.g[j], h[kk], v[e]);
+        }
+      }
+      const int iy = 2 * ky0 + r, ix = 2 * kx0 + 4 * p;
+      if (iy < ny && ix < nx)
+        *reinterpret_cast<float4*>(out + (long long)iy * nx + ix) = make_float4(v[0], v[1], v[2], v[3]);
+    }
   }
+}
+
+// Resident CTAs of a 256-thread kernel with `smem` bytes of dynamic shared
+// memory on the current device (the attribute set once per kernel).
+int resident_ctas(const void* fn, int smem) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per * sms;
+}
+
+// CTAs for `work` (column, plane) units of a 3D level: every resident CTA, but
+// at least four planes each.
+int grid3d(long long work, int cap) {
+  const long long g = (work + 3) / 4;
+  return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+// Launch with programmatic stream serialization (the kernel waits on the
+// previous grid itself, griddep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int L>
+cudaError_t launch_a2(cudaStream_t st, const float* in, int nx, int ny, float* A, float* H, float* V, float* D,
+                      float wdet, const Filt& f) {
+  static std::once_flag once;
+  static int cap = 0;
+  std::call_once(once, [] { cap = resident_ctas((const void*)dwt2d_analysis_fast_kernel<L>, A2F<L>::SMEM); });
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const int tx = ((nx >> 1) + A2F<L>::OX - 1) / A2F<L>::OX, ty = ((ny >> 1) + A2F<L>::OY - 1) / A2F<L>::OY;
+  const int ntiles = tx * ty;
+  return launch_pdl(dwt2d_analysis_fast_kernel<L>, ntiles < cap ? ntiles : cap, A2F<L>::SMEM, st, in, nx, ny, A, H, V,
+                    D, wdet, f, tx, ntiles);
+}
+
+template <int L>
+cudaError_t launch_s2(cudaStream_t st, const float* A, const float* H, const float* V, const float* D, float wdet,
+                      int nx, int ny, float* out, const Filt& f) {
+  static std::once_flag once;
+  static int cap = 0;
+  std::call_once(once, [] { cap = resident_ctas((const void*)dwt2d_synthesis_fast_kernel<L>, S2F<L>::SMEM); });
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const int tx = ((nx >> 1) + S2F<L>::OX - 1) / S2F<L>::OX, ty = ((ny >> 1) + S2F<L>::OY - 1) / S2F<L>::OY;
+  const int ntiles = tx * ty;
+  return launch_pdl(dwt2d_synthesis_fast_kernel<L>, ntiles < cap ? ntiles : cap, S2F<L>::SMEM, st, A, H, V, D, wdet,
+                    nx, ny, out, f, tx, ntiles);
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -397,9 +516,6 @@ __device__ __forceinline__ const float* band_sel(const CBands8& b, int c) {
   return c == 0 ? b.p[0] : c == 1 ? b.p[1] : c == 2 ? b.p[2] : c == 3 ? b.p[3]
        : c == 4 ? b.p[4] : c == 5 ? b.p[5] : c == 6 ? b.p[6] : b.p[7];
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int L>
 struct A3F {
@@ -415,7 +531,8 @@ struct A3F {
 
 template <int L>
 __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
-                                                                  const Bands8 out, float wdet, int cz, const Filt f) {
+                                                                  const Bands8 out, float wdet, const Filt f,
+                                                                  int cols_x, int ncols) {
   using G = A3F<L>;
   extern __shared__ __align__(16) unsigned char dsm[];  // G::SMEM bytes (more than the static 48 KB)
   auto slab = reinterpret_cast<float(*)[G::WY][G::WX]>(dsm);
@@ -426,8 +543,29 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
                                                                                              // the last L planes
   const int t = threadIdx.x;
   const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
-  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
-  const int kz1 = min(kz0 + cz, nz2);
+  griddep_wait();
+  griddep_trigger();
+  // this thread's y-pass output: quarter qq (xb = qq & 1, yb = qq >> 1), row ky, columns 4 qx .. 4 qx + 3
+  const int qq = t / 64, ky = (t / 8) % 8, qx = t % 8;
+  const int xb = qq & 1, yb = qq >> 1;
+  const float(*src)[G::OX] = xb ? xh : xl;
+  float2 fy[L];  // the y filter of this quarter, packed
+#pragma unroll
+  for (int j = 0; j < L; ++j) fy[j] = dup2(yb ? f.g[j] : f.h[j]);
+  float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
+  float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
+  const float2 wlo = dup2(qq == 0 ? 1.f : wdet), whi = dup2(wdet);
+  // this CTA's share of the (column, output plane) work, z fastest: whole runs of one column, so a
+  // z halo is staged again only where the share crosses into the next column
+  const long long W = (long long)ncols * nz2;
+  const long long w_end = W * (blockIdx.x + 1) / gridDim.x;
+  for (long long w = W * blockIdx.x / gridDim.x; w < w_end;) {
+  const int colid = (int)(w / nz2);
+  const int kz0 = (int)(w - (long long)colid * nz2);
+  const int kz1 = (int)(w_end - w < (long long)(nz2 - kz0) ? kz0 + (w_end - w) : nz2);
+  w += kz1 - kz0;
+  const int kx0 = (colid % cols_x) * G::OX, ky0 = (colid / cols_x) * G::OY;
+  __syncthreads();  // the previous run is done with the shared buffers
   const int nplanes = 2 * (kz1 - kz0) + L - 2;  // input planes 2 kz0 .. 2 kz1 + L - 3 (periodic)
   const bool interior_xy = 2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny;
   const float* col0 = in + (long long)(2 * ky0) * nx + 2 * kx0;
@@ -455,18 +593,8 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
   };
 #pragma unroll
   for (int pl = 0; pl < G::NSLOT - 1; ++pl) load(pl);
-  // this thread's y-pass output: quarter qq (xb = qq & 1, yb = qq >> 1), row ky, columns 4 qx .. 4 qx + 3
-  const int qq = t / 64, ky = (t / 8) % 8, qx = t % 8;
-  const int xb = qq & 1, yb = qq >> 1;
-  const float(*src)[G::OX] = xb ? xh : xl;
-  float2 fy[L];  // the y filter of this quarter, packed
-#pragma unroll
-  for (int j = 0; j < L; ++j) fy[j] = dup2(yb ? f.g[j] : f.h[j]);
   const int oy = ky0 + ky, ox = kx0 + 4 * qx;
   const bool store = oy < ny2 && ox < nx2;
-  float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
-  float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
-  const float2 wlo = dup2(qq == 0 ? 1.f : wdet), whi = dup2(wdet);
   for (int pl = 0; pl < nplanes; ++pl) {
     load(pl + G::NSLOT - 1);
     cp_async_wait_group<G::NSLOT - 1>();  // this thread's copies of plane pl have landed
@@ -522,6 +650,7 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
       }
     }
   }
+  }  // runs
 }
 
 template <int L>
@@ -542,16 +671,27 @@ struct S3F {
 // plane 2m + e is then sum_jj h_{2jj+e} P_lo(m - jj) + g_{2jj+e} P_hi(m - jj).
 template <int L>
 __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
-                                                                   int nz, float* __restrict__ out, int cz,
-                                                                   const Filt f) {
+                                                                   int nz, float* __restrict__ out, const Filt f,
+                                                                   int cols_x, int ncols) {
   using G = S3F<L>;
   __shared__ __align__(16) float cw[G::NSLOT][8][G::WY][G::WX];
   __shared__ __align__(16) float yl[2][2 * G::OY][G::WX];
   __shared__ __align__(16) float yh[2][2 * G::OY][G::WX];
   const int t = threadIdx.x;
   const int cx = nx >> 1, cy = ny >> 1, cz2 = nz >> 1;
-  const int kx0 = blockIdx.x * G::OX, ky0 = blockIdx.y * G::OY, kz0 = blockIdx.z * cz;
-  const int kz1 = min(kz0 + cz, cz2);
+  griddep_wait();
+  griddep_trigger();
+  const int pr = t / 16, pq = t % 16;  // this thread's pixel row and quad (x-pass, z-pass, store)
+  // this CTA's share of the (column, coefficient plane) work, z fastest (as in the analysis)
+  const long long W = (long long)ncols * cz2;
+  const long long w_end = W * (blockIdx.x + 1) / gridDim.x;
+  for (long long w = W * blockIdx.x / gridDim.x; w < w_end;) {
+  const int colid = (int)(w / cz2);
+  const int kz0 = (int)(w - (long long)colid * cz2);
+  const int kz1 = (int)(w_end - w < (long long)(cz2 - kz0) ? kz0 + (w_end - w) : cz2);
+  w += kz1 - kz0;
+  const int kx0 = (colid % cols_x) * G::OX, ky0 = (colid / cols_x) * G::OY;
+  __syncthreads();  // the previous run is done with the shared buffers
   const int nplanes = kz1 - kz0 + G::LH;  // coefficient planes kz0 - LH .. kz1 - 1 (periodic)
   const bool interior_xy = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= cx && ky0 + G::OY <= cy;
   auto load = [&](int pl) {
@@ -569,8 +709,7 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
   };
 #pragma unroll
   for (int pl = 0; pl < G::NSLOT - 1; ++pl) load(pl);
-  const int pr = t / 16, pq = t % 16;  // this thread's pixel row and quad (x-pass, z-pass, store)
-  float4 rlo[L / 2], rhi[L / 2];       // P_lo, P_hi of the last L/2 coefficient planes, oldest first
+  float4 rlo[L / 2], rhi[L / 2];  // P_lo, P_hi of the last L/2 coefficient planes, oldest first
 #pragma unroll
   for (int j = 0; j < L / 2; ++j) rlo[j] = rhi[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int pl = 0; pl < nplanes; ++pl) {
@@ -664,31 +803,35 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
       }
     }
   }
+  }  // runs
 }
 
 template <int L>
-cudaError_t launch_a3(dim3 grid, cudaStream_t st, const float* in, int nx, int ny, int nz, const Bands8& b, float wdet,
-                      int cz, const Filt& f) {
+cudaError_t launch_a3(cudaStream_t st, const float* in, int nx, int ny, int nz, const Bands8& b, float wdet,
+                      const Filt& f) {
   static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(dwt3d_analysis_fast_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                A3F<L>::SMEM);
-  });
-  if (attr != cudaSuccess) return attr;
-  dwt3d_analysis_fast_kernel<L><<<grid, A3F<L>::THREADS, A3F<L>::SMEM, st>>>(in, nx, ny, nz, b, wdet, cz, f);
-  return cudaGetLastError();
+  static int cap = 0;
+  std::call_once(once, [] { cap = resident_ctas((const void*)dwt3d_analysis_fast_kernel<L>, A3F<L>::SMEM); });
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const int cols_x = ((nx >> 1) + A3F<L>::OX - 1) / A3F<L>::OX;
+  const int ncols = cols_x * (((ny >> 1) + A3F<L>::OY - 1) / A3F<L>::OY);
+  const long long work = (long long)ncols * (nz >> 1);
+  return launch_pdl(dwt3d_analysis_fast_kernel<L>, grid3d(work, cap), A3F<L>::SMEM, st, in, nx, ny, nz, b, wdet, f,
+                    cols_x, ncols);
 }
 
-// z planes per CTA for a level with coefficient-column count `cols` and
-// nz2 coefficient planes: chunks of 16 planes, halved (down to 4) until the
-// grid has at least three CTAs per SM.
-int chunk3d(long long cols, int nz2) {
-  int dev = 0, sms = 148;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int cz = 16;
-  while (cz > 4 && cols * ((nz2 + cz - 1) / cz) < 3LL * sms) cz >>= 1;
-  return cz < nz2 ? cz : nz2;
+template <int L>
+cudaError_t launch_s3(cudaStream_t st, const CBands8& b, float wdet, int nx, int ny, int nz, float* out,
+                      const Filt& f) {
+  static std::once_flag once;
+  static int cap = 0;
+  std::call_once(once, [] { cap = resident_ctas((const void*)dwt3d_synthesis_fast_kernel<L>, 0); });
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const int cols_x = ((nx >> 1) + S3F<L>::OX - 1) / S3F<L>::OX;
+  const int ncols = cols_x * (((ny >> 1) + S3F<L>::OY - 1) / S3F<L>::OY);
+  const long long work = (long long)ncols * (nz >> 1);
+  return launch_pdl(dwt3d_synthesis_fast_kernel<L>, grid3d(work, cap), 0, st, b, wdet, nx, ny, nz, out, f, cols_x,
+                    ncols);
 }
 
 // ------------------------------------------------- separable 1D (3D grids)
@@ -779,11 +922,9 @@ cudaError_t dwt2d_analysis_level(const float* in, int nx, int ny, float* approx,
   const Filt f = make_filt(h, g, L);
   if (nx % 8 == 0 && ny % 2 == 0 && aligned16(in) && aligned16(approx) && aligned16(bandH) && aligned16(bandV) &&
       aligned16(bandD) && (L == 2 || L == 4 || L == 8)) {
-    dim3 grid(((nx >> 1) + 63) / 64, ((ny >> 1) + 15) / 16);
-    if (L == 2) dwt2d_analysis_fast_kernel<2><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
-    if (L == 4) dwt2d_analysis_fast_kernel<4><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
-    if (L == 8) dwt2d_analysis_fast_kernel<8><<<grid, 256, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
-    return cudaGetLastError();
+    if (L == 2) return launch_a2<2>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
+    if (L == 4) return launch_a2<4>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
+    return launch_a2<8>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
   }
   dim3 grid(((nx >> 1) + A_OX - 1) / A_OX, ((ny >> 1) + A_OY - 1) / A_OY);
   dwt2d_analysis_kernel<<<grid, A_THREADS, 0, st>>>(in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
@@ -796,11 +937,9 @@ cudaError_t dwt2d_synthesis_level(const float* approx, const float* bandH, const
   const Filt f = make_filt(h, g, L);
   if (nx % 8 == 0 && ny % 2 == 0 && aligned16(approx) && aligned16(bandH) && aligned16(bandV) && aligned16(bandD) &&
       aligned16(out) && (L == 2 || L == 4 || L == 8)) {
-    dim3 grid(((nx >> 1) + 63) / 64, ((ny >> 1) + 15) / 16);
-    if (L == 2) dwt2d_synthesis_fast_kernel<2><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
-    if (L == 4) dwt2d_synthesis_fast_kernel<4><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
-    if (L == 8) dwt2d_synthesis_fast_kernel<8><<<grid, 256, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
-    return cudaGetLastError();
+    if (L == 2) return launch_s2<2>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
+    if (L == 4) return launch_s2<4>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
+    return launch_s2<8>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
   }
   dim3 grid((nx + S_OX - 1) / S_OX, (ny + S_OY - 1) / S_OY);
   dwt2d_synthesis_kernel<<<grid, S_THREADS, 0, st>>>(approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
@@ -837,13 +976,9 @@ cudaError_t dwt3d_analysis_level(const float* in, int nx, int ny, int nz, float*
     b.p[c] = bands[c];
   }
   const Filt f = make_filt(h, g, L);
-  const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
-  const long long cols = (long long)((nx2 + 31) / 32) * ((ny2 + 7) / 8);
-  const int cz = chunk3d(cols, nz2);
-  dim3 grid((nx2 + 31) / 32, (ny2 + 7) / 8, (nz2 + cz - 1) / cz);
-  if (L == 2) return launch_a3<2>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
-  if (L == 4) return launch_a3<4>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
-  return launch_a3<8>(grid, st, in, nx, ny, nz, b, wdet, cz, f);
+  if (L == 2) return launch_a3<2>(st, in, nx, ny, nz, b, wdet, f);
+  if (L == 4) return launch_a3<4>(st, in, nx, ny, nz, b, wdet, f);
+  return launch_a3<8>(st, in, nx, ny, nz, b, wdet, f);
 }
 
 cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int nx, int ny, int nz, float* out,
@@ -856,14 +991,9 @@ cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int n
     b.p[c] = bands[c];
   }
   const Filt f = make_filt(h, g, L);
-  const int cx = nx >> 1, cy = ny >> 1, cz2 = nz >> 1;
-  const long long cols = (long long)((cx + 31) / 32) * ((cy + 7) / 8);
-  const int cz = chunk3d(cols, cz2);
-  dim3 grid((cx + 31) / 32, (cy + 7) / 8, (cz2 + cz - 1) / cz);
-  if (L == 2) dwt3d_synthesis_fast_kernel<2><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
-  if (L == 4) dwt3d_synthesis_fast_kernel<4><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
-  if (L == 8) dwt3d_synthesis_fast_kernel<8><<<grid, 256, 0, st>>>(b, wdet, nx, ny, nz, out, cz, f);
-  return cudaGetLastError();
+  if (L == 2) return launch_s3<2>(st, b, wdet, nx, ny, nz, out, f);
+  if (L == 4) return launch_s3<4>(st, b, wdet, nx, ny, nz, out, f);
+  return launch_s3<8>(st, b, wdet, nx, ny, nz, out, f);
 }
 
 cudaError_t scale_copy_launch(float* dst, const float* src, long long n, float w, cudaStream_t st) {

@@ -36,12 +36,40 @@ __device__ __forceinline__ float stencil_cell(const float4 (&win)[2 * R + 1], co
   return acc;
 }
 
+// stencil_cell for all four columns in packed FP32x2 arithmetic (pairs of columns 0-1, 2-3); each
+// lane takes the scalar function's operations in the same order, so acc[j] equals stencil_cell(.., j, ..).
+template <int R, bool DIFF>
+__device__ __forceinline__ void stencil_cells2(const float4 (&win)[2 * R + 1], const float (&f)[20],
+                                               const float2 (&w2)[R + 1], float (&acc)[4]) {
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 c = make_float2(f[8 + 2 * p], f[9 + 2 * p]);
+    const float2 nc = __fmul2_rn(c, dup2(-1.f));
+    float2 a2 = dup2(0.f);
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+      const float2 up = p ? hi2(win[R + m]) : lo2(win[R + m]);
+      const float2 dn = p ? hi2(win[R - m]) : lo2(win[R - m]);
+      a2 = __ffma2_rn(w2[m], pair_term2<DIFF>(up, dn, c, nc), a2);
+    }
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+      const float2 rt = make_float2(f[8 + 2 * p + m], f[9 + 2 * p + m]);
+      const float2 lt = make_float2(f[8 + 2 * p - m], f[9 + 2 * p - m]);
+      a2 = __ffma2_rn(w2[m], pair_term2<DIFF>(rt, lt, c, nc), a2);
+    }
+    acc[2 * p] = a2.x;
+    acc[2 * p + 1] = a2.y;
+  }
+}
+
 // Laplacian of the 4 x RUN cells a thread owns in a box (pitch BW floats, R halo rows above the tile,
 // the thread's columns at XH + c0): lo[rr][j] for row r0 + rr.  For the low part of a compensated
 // pair (a field of the order of the rounding error of its high part), so it takes the cheapest form,
 // sum_m w_m (a + b) - w_c c with the centre weight w_c = 4 sum_m w_m summed in FP32 (R additions and
 // a multiply, so up to R + 1 roundings): 2 FP operations per tap; the rounded w_c departs from a
 // zero-sum stencil by a relative ~R 2^-24 of a field that is itself ~2^-24 of the state.
+// (Packed FP32x2 arithmetic, pairs of columns 0-1 and 2-3, each lane in the scalar operation order.)
 template <int R, int RUN, int BW, int XH>
 __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r0, int c0,
                                             const float* __restrict__ w, float (&lo)[RUN][4]) {
@@ -49,6 +77,10 @@ __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r
 #pragma unroll
   for (int m = 1; m <= R; ++m) wc += w[m];
   wc *= 4.f;
+  const float2 nwc = dup2(-wc);
+  float2 w2[R + 1];
+#pragma unroll
+  for (int m = 0; m <= R; ++m) w2[m] = dup2(w[m]);
   float4 win[2 * R + 1];
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) win[i] = *reinterpret_cast<const float4*>(box + (r0 + i) * BW + XH + c0);
@@ -58,13 +90,22 @@ __device__ __forceinline__ void stencil_run(const float* __restrict__ box, int r
     float f[20];
     load_row20(box + (r0 + rr + R) * BW + c0 + XH - 8, f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float acc = -wc * f[8 + j];
+    for (int p = 0; p < 2; ++p) {
+      float2 acc = __fmul2_rn(nwc, make_float2(f[8 + 2 * p], f[9 + 2 * p]));
 #pragma unroll
-      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], f4get(win[R + m], j) + f4get(win[R - m], j), acc);
+      for (int m = 1; m <= R; ++m) {
+        const float2 up = p ? hi2(win[R + m]) : lo2(win[R + m]);
+        const float2 dn = p ? hi2(win[R - m]) : lo2(win[R - m]);
+        acc = __ffma2_rn(w2[m], __fadd2_rn(up, dn), acc);
+      }
 #pragma unroll
-      for (int m = 1; m <= R; ++m) acc = fmaf(w[m], f[8 + j + m] + f[8 + j - m], acc);
-      lo[rr][j] = acc;
+      for (int m = 1; m <= R; ++m)
+        acc = __ffma2_rn(w2[m],
+                         __fadd2_rn(make_float2(f[8 + 2 * p + m], f[9 + 2 * p + m]),
+                                    make_float2(f[8 + 2 * p - m], f[9 + 2 * p - m])),
+                         acc);
+      lo[rr][2 * p] = acc.x;
+      lo[rr][2 * p + 1] = acc.y;
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];

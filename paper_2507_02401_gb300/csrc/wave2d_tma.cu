@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const Step
   if (t == 0 && first < ntiles) issue(first, 0);
 
   const float ckh = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
+  float2 w2[R + 1];  // stencil weights, packed
+#pragma unroll
+  for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
   int k = 0;
   bool ok = true;
   int issued = (first < ntiles) ? 1 : 0;
@@ -182,12 +185,14 @@ __global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const Step
         }
         float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f);  // adjoint: own Z_lo cells
         if (ADJ) zl4 = *reinterpret_cast<const float4*>(PL + brow * BW + XH + c0);
+        // forward: zero-sum pair form (a + b) - 2c per tap; adjoint: difference form on Z
+        float st4[4];
+        stencil_cells2<R, ADJ>(win, f, w2, st4);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float c = f[8 + j];  // own P or Z
           if (!ADJ) {
-            // zero-sum pair form (a + b) - 2c per tap: 3 FP operations instead of 4
-            const float acc = stencil_cell<R, false>(win, f, j, a.w);
+            const float acc = st4[j];
             const float inc = VARC ? fmaf(a.c_lap * f4get(kh4[rr], j), acc, (a.c_lap * f4get(kl4[rr], j)) * acc)
                                    : fmaf(ckh, acc, ckl * acc);
             if (!LAYER) {
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const Step
             pn[j] = c + dn[j];
             pl[j] = 0.f;
           } else {
-            const float acc = stencil_cell<R, true>(win, f, j, a.w) + lo[rr][j];
+            const float acc = st4[j] + lo[rr][j];
             const float g = f4get(d4[rr], j) + a.c_lap * acc;  // G' (S^T r injected into G beforehand)
             const float zl = f4get(zl4, j);
             dn[j] = g;

@@ -151,7 +151,7 @@ class Plan:
 
 
 class Batch:
-    """Many 2D constant-medium plans advanced together by the batched engine
+    """Many 2D plans (one stencil order) advanced together by the batched engine
     (all instances' tiles in one table; tile height and launch form -- one
     launch per time step, or one cooperative launch per K / K* -- chosen by
     the library's autotuner when the batch is created).  The plans must
