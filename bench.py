@@ -16,8 +16,9 @@ instance (weak scaling, no data-path collective).
 
 --workload vessels times the 2D 512 x 512 workload instead: smooth random
 speed of sound in [1400, 1600] m/s, order-8 stencil, 1500 time samples, 512
-sensors on a circle, db4 with 5 levels, 100 CG iterations per step, steps
-cycling through s in {1, 2} x alpha in {1e-3, 1e-2}.
+sensors on a circle, db4 with 5 levels; one step = its four reconstructions
+(s in {1, 2} x alpha in {1e-3, 1e-2}, 100 CG iterations each) through
+pat_solve_multi, two right-hand sides per persistent wave launch.
 
 --workload batch64 times 64 independent reconstructions of uneven size
 (n in {128..512}, order 8, 50 CG iterations each) through the batched
@@ -386,8 +387,17 @@ def run_ours(args):
     x = torch.empty(w.shape, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
     flush.zero_()  # first use outside the timed region (the first launch of a kernel loads its module)
+    # several (s, alpha) combinations: one step solves all of them with pat_solve_multi (two right-hand
+    # sides per wave launch on the persistent engine); one combination: pat_solve
+    multi = len(combos) > 1
+    xs_multi = [torch.empty(w.shape, device="cuda") for _ in combos]
+    iters_per_step = w.iters * (len(combos) if multi else 1)
 
     def solve(k, yy=y, xx=x, uu=u):
+        if multi:
+            _lib.pat_solve_multi(plan.handle, [yy] * len(combos), [a for _, a in combos], [s for s, _ in combos],
+                                 w.iters, xs_multi, stream)
+            return
         s, alpha = combos[k % len(combos)]
         _lib.pat_solve(plan.handle, yy, alpha, s, w.iters, None, uu, xx, None, stream)
 
@@ -421,35 +431,46 @@ def run_ours(args):
     y_host = torch.empty((w.ns, w.nt), dtype=torch.float32, pin_memory=True)
     y_host.copy_(torch.as_tensor(y_np))
     x_host = torch.empty(w.shape, dtype=torch.float32, pin_memory=True)
+    xs_host = [torch.empty(w.shape, dtype=torch.float32, pin_memory=True) for _ in combos]
     yh, xh = y_host.numpy(), x_host.numpy()
+    y_dev = torch.empty((w.ns, w.nt), device="cuda")
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        s, alpha = combos[k % len(combos)]
-        _lib.pat_solve(plan.handle, yh, alpha, s, w.iters, None, None, xh, None, stream)
+        if multi:  # pat_solve_multi takes device arrays: the copies are inside the timed region
+            y_dev.copy_(y_host, non_blocking=True)
+            solve(k, yy=y_dev)
+            for xhm, xd in zip(xs_host, xs_multi):
+                xhm.copy_(xd, non_blocking=True)
+        else:
+            s, alpha = combos[k % len(combos)]
+            _lib.pat_solve(plan.handle, yh, alpha, s, w.iters, None, None, xh, None, stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, True)
     barrier(world)
 
-    iters_total = world * args.steps * w.iters
-    value = job_throughput(args.steps * w.iters, world, t_ms)
+    iters_total = world * args.steps * iters_per_step
+    value = job_throughput(args.steps * iters_per_step, world, t_ms)
     bytes_per_pt = 16 if plan_varc(w) else 12
-    # the persistent engine runs a whole K or K* per launch, the step engines one time step
+    # the persistent engine runs a whole K or K* per launch (two fields at once under pat_solve_multi),
+    # the step engines one time step; achieved = the library's point-updates x algorithmic bytes over the
+    # device time of its wave launches
     steps_per_launch = (w.nt - 1) if plan.path == 1 else 1
     launches = wave_calls * (w.nt - 1) // steps_per_launch
-    per_launch_bytes = bytes_per_pt * w.N * steps_per_launch
     launch_ms = wave_ms / max(launches, 1)
-    achieved = per_launch_bytes / (launch_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
+    achieved = bytes_per_pt * points / (wave_ms / 1e3) / 1e9 if wave_ms > 0 else 0.0
     peak, peak_kind = peaks()
     traffic, digest = kernel_traffic(args.workload)
     engine = {1: "persistent", 2: "step"}.get(plan.path, "?")
-    gpts = world * args.steps * (2 * w.iters + 1) * (w.nt - 1) * w.N / (t_ms / 1e3) / 1e9
+    gpts = world * args.steps * (2 * w.iters + 1) * (len(combos) if multi else 1) * (w.nt - 1) * w.N / (t_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": spec["desc"], "engine": engine, "iters_per_step": w.iters,
+        "config": {"workload": spec["desc"], "engine": engine, "iters_per_step": iters_per_step,
+                   "solves_per_step": len(combos) if multi else 1,
+                   "right_hand_sides_per_wave_launch": 2 if (multi and plan.path == 1) else 1,
                    "l2": "256 MiB buffer written before every step (inside the timed region)",
                    "parallelism": f"replicas x{world} (independent instances per rank)"},
         "gpoint_updates_per_s": gpts,
@@ -458,12 +479,13 @@ def run_ours(args):
                      "kernel": f"{spec['kernel']} ({engine} engine)",
                      "algorithmic_bytes_per_point_update": bytes_per_pt,
                      "launch_ms": launch_ms, "launches_timed": launches,
-                     "launch": "one K or K* application" if steps_per_launch > 1 else
+                     "launch": ("one K or K* application of two right-hand sides" if multi else
+                                "one K or K* application") if steps_per_launch > 1 else
                                "one time step (averaged over whole K / K* applications, sampling and "
                                "injection launches included)",
                      "source_sha256_16": digest},
         "e2e": {"value": iters_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_np.nbytes),
-                "d2h_bytes_per_step": int(w.N * 4)},
+                "d2h_bytes_per_step": int(w.N * 4 * (len(combos) if multi else 1))},
         "gpu_launches": int(kernels + args.steps),  # library kernels + one L2 flush per step
         "clocks": clocks,
     }

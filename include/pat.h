@@ -183,6 +183,27 @@ pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, dou
                                float* u, float* x, double* J, void* stream);
 
 /*
+ * pat_solve_multi — nrhs pat_solve problems on one plan (same grid, medium
+ * and sensors; each with its own data ys[r], alphas[r], ss[r]; u0 = 0; a
+ * common iteration count), advanced two at a time: on the persistent engine
+ * (no absorbing layer) every K and every K* of a pair runs as one launch
+ * carrying both fields, so the pair shares each time step's halo exchange
+ * and barrier (the paper's CG of Sec. 4 applied to several regularisations
+ * of one measurement, e.g. a sweep over alpha and s).  Each right-hand side
+ * gets exactly the result pat_solve gives it.  Other engines run the
+ * problems one after the other.
+ *   ys, xs   host arrays of nrhs DEVICE pointers (Ns*nt floats in, N floats
+ *            out: x = E_s u after `iters` CG iterations).
+ *   alphas, ss  host arrays of nrhs doubles (alpha > 0, s finite).
+ * Asynchronous on `stream`; device status through pat_plan_check.  The first
+ * call with nrhs >= 2 allocates the second right-hand side's buffers.
+ * Errors: PAT_ERR_INVALID (NULL or host arrays, nrhs < 1, bad alpha / s),
+ * PAT_ERR_CUDA, PAT_ERR_OOM.
+ */
+pat_status pat_solve_multi(pat_plan* plan, int nrhs, const float* const* ys, const double* alphas,
+                           const double* ss, int iters, float* const* xs, void* stream);
+
+/*
  * pat_objective — the Tikhonov functional whose minimiser pat_solve computes
  * (paper Sec. 3, the variational problem behind Eq. (linear_minimization),
  * in wavelet coefficients):

@@ -46,6 +46,7 @@ SIGNATURES = [
                                 c_void_p]),
     ("pat_solve_landweber", c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    ("pat_solve_multi", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     ("pat_objective", c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, ctypes.POINTER(c_double),
                               c_void_p, c_void_p]),
     ("pat_solve_batched", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
@@ -294,6 +295,19 @@ def pat_EsT_noalloc(nx, ny, family, levels, level_offset, s, x, u, stream=None):
                                  f"{int(nx) * int(ny)} elements (got {t.dtype}, {t.device}, {t.numel()})")
     return _check(load().pat_EsT_noalloc(int(nx), int(ny), int(family), int(levels), int(level_offset), float(s),
                                          ptr(x), ptr(u), stream_handle(stream)))
+
+
+def pat_solve_multi(plan, ys, alphas, ss, iters, xs, stream=None):
+    """Several CG solves of one plan, two per wave launch on the persistent
+    engine (device arrays only); returns the status."""
+    n = len(ys)
+    if not (len(xs) == len(alphas) == len(ss) == n):
+        raise ValueError("ys, alphas, ss and xs must have the same length")
+    yp = (c_void_p * n)(*[ptr(y) for y in ys])
+    xp = (c_void_p * n)(*[ptr(x) for x in xs])
+    ap = (c_double * n)(*[float(a) for a in alphas])
+    sp = (c_double * n)(*[float(v) for v in ss])
+    return _check(load().pat_solve_multi(plan, n, yp, ap, sp, int(iters), xp, stream_handle(stream)))
 
 
 def pat_objective(plan, y, alpha, s, u, grad=None, stream=None):

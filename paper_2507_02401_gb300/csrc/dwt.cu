@@ -445,11 +445,11 @@ int resident_ctas(const void* fn, int smem) {
   return per * sms;
 }
 
-// CTAs for `work` (column, plane) units of a 3D level: every resident CTA, but
-// at least four planes each.
+// CTAs for `work` (column, plane) units of a 3D level: every resident CTA,
+// down to one output plane each on the small levels (a CTA walks its planes
+// one after the other, so short runs on many CTAs beat long runs on few).
 int grid3d(long long work, int cap) {
-  const long long g = (work + 3) / 4;
-  return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+  return (int)(work < cap ? (work < 1 ? 1 : work) : cap);
 }
 
 // Launch with programmatic stream serialization (the kernel waits on the

@@ -82,6 +82,10 @@ struct Persist2DArgs {
   int poll_ns;           // back-off between polls of the exchange (0 = spin)
   const float* sp_a;     // absorbing layer: per-cell factors a, b of the damped update (nullptr = none)
   const float* sp_b;
+  // second right-hand side (the two-field kernel only)
+  const float* in1;
+  float* out1;
+  float* part1;
 };
 
 // Arguments of the per-step kernels.
@@ -137,9 +141,12 @@ bool persist2d_supported(int R, bool varc);
 int persist2d_tile_x();
 int persist2d_tile_y();
 size_t persist2d_smem_bytes(int R, bool adj);
-size_t persist2d_xbuf_words(int R, bool adj, int ntiles);  // 64-bit exchange words
+size_t persist2d_xbuf_words(int R, bool adj, int ntiles, int nr = 1);  // 64-bit exchange words, nr fields
 int persist2d_max_ctas(int R, bool adj, bool varc);  // co-resident CTA limit on this device
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
+// Two right-hand sides per launch (no absorbing layer): a.in / a.out and a.in1 / a.out1.
+int persist2d_max_ctas2(int R, bool adj, bool varc);
+cudaError_t persist2d_launch2(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
 // the same with the absorbing layer (a.sp_a, a.sp_b set)
 cudaError_t persist2d_launch_layer(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st);
 cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, int nsplit, int nt, float* y,
@@ -149,9 +156,10 @@ cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, 
 bool tma3d_supported(int nx, int R, bool varc);
 // `cur` (80 x (16+2R) x 1 boxes) and `prev` (64 x 16 x 1) descriptors of an nx x ny x nz float field
 cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev);
-int tma3d_zchunk(int nx, int ny, int nz);
-long long tma3d_threads(int nx, int ny, int nz, int zchunk);  // threads of one launch (fused sampling)
-cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+int tma3d_ctas(int R, int nx, int ny, int nz);  // CTAs of a step launch (one wave, equal shares)
+int tma3d_cta_of(int nx, int ny, int nz, int nctas, int x, int y, int z);  // CTA whose share holds a cell
+long long tma3d_threads(int nctas);  // threads of one launch (fused sampling)
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
                               int* status, long long timeout_ns, cudaStream_t st);
 
 // wave2d_tma.cu: 2D increment-form step with TMA tile pipelines (forward; constant-medium adjoint)

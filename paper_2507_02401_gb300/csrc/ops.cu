@@ -1,4 +1,5 @@
 // Operators and solver behind the C ABI: K, K*, E_s, E_s*, CG.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -136,7 +137,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     b.inj_r = nullptr;
     e = step2d_launch(p->R, adj, b, st);
   } else if (p->tma3d && tma_ready(p, a)) {
-    const long long nthr = tma3d_threads(p->n[0], p->n[1], p->n[2], p->tma3d_zchunk);
+    const long long nthr = tma3d_threads(p->tma3d_ctas);
     if (y && a.ns > nthr) a.y = nullptr;
     if (a.inj_r) {  // the adjoint's post-step injection, fused per CTA
       a.inj_tile_ptr = p->d_tinj3_ptr;
@@ -154,7 +155,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
       if (!dp) return cudaErrorInvalidValue;
       mp = dp->own;
     }
-    e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_zchunk, p->d_status, p->timeout_ns, st);
+    e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_ctas, p->d_status, p->timeout_ns, st);
   } else {
     const long long nthr =
         (long long)((p->n[0] + 31) / 32) * ((p->n[1] + 15) / 16) * ((p->n[2] + 31) / 32) * 128;
@@ -692,6 +693,143 @@ pat_status solve_device(pat_plan* p, const float* y, double alpha, double s, int
   return PAT_OK;
 }
 
+// ------------------------------------------------ several right-hand sides
+// Buffers of the second right-hand side and the two-field exchange strips.
+static pat_status multi_setup(pat_plan* p, cudaStream_t st) {
+  if (p->m2.ready) return PAT_OK;
+  auto fl = [&](float** q, size_t n, const char* what) {
+    return plan_alloc(p, reinterpret_cast<void**>(q), std::max<size_t>(n, 1) * sizeof(float), what);
+  };
+  const size_t N = (size_t)p->N, M = (size_t)p->ns * p->nt;
+  PAT_TRY(fl(&p->m2.r, N, "cg r (second right-hand side)"));
+  PAT_TRY(fl(&p->m2.p, N, "cg p (second right-hand side)"));
+  PAT_TRY(fl(&p->m2.q, N, "cg q (second right-hand side)"));
+  PAT_TRY(fl(&p->m2.img, N, "image buffer (second right-hand side)"));
+  PAT_TRY(fl(&p->m2.u, N, "cg u (second right-hand side)"));
+  PAT_TRY(fl(&p->m2.ybuf, M, "sensor data buffer (second right-hand side)"));
+  PAT_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->m2.sc), sizeof(CgScalars), "cg scalars (second)"));
+  PAT_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->m2.partials), sizeof(double) * cg_grid_blocks(),
+                     "cg partials (second)"));
+  PAT_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->m2.counter), sizeof(unsigned), "cg counter (second)"));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->m2.counter, 0, sizeof(unsigned), st));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->m2.sc, 0, sizeof(CgScalars), st));
+  p->m2.two_field = false;
+  if (p->path == PAT_PATH_PERSISTENT && p->sponge_w == 0 &&
+      persist2d_max_ctas2(p->R, false, p->varc) >= p->ntiles && persist2d_max_ctas2(p->R, true, p->varc) >= p->ntiles) {
+    PAT_TRY(fl(&p->m2.part, (size_t)4 * p->nsplit * p->nt, "split sensor parts (second)"));
+    p->m2.xbuf_bytes = persist2d_xbuf_words(p->R, true, p->ntiles, 2) * 8;
+    PAT_TRY(plan_alloc(p, &p->m2.xbuf, p->m2.xbuf_bytes, "two-field exchange strips"));
+    p->m2.two_field = true;
+  }
+  p->m2.ready = true;
+  return PAT_OK;
+}
+
+static bool two_field(const pat_plan* p) {
+  return p->m2.ready && p->m2.two_field && p->path == PAT_PATH_PERSISTENT && p->sponge_w == 0;
+}
+
+// K on two right-hand sides: one two-field persistent launch, else two applications.
+static pat_status wave_forward2(pat_plan* p, const float* x0, const float* x1, float* y0, float* y1,
+                                cudaStream_t st) {
+  if (!two_field(p)) {
+    PAT_TRY(wave_forward(p, x0, y0, st));
+    return wave_forward(p, x1, y1, st);
+  }
+  if (p->prof_on) PAT_TRY(prof_mark(p, st));
+  Persist2DArgs a = persist_args(p);
+  a.in = x0;
+  a.out = y0;
+  a.in1 = x1;
+  a.out1 = y1;
+  a.part1 = p->m2.part;
+  a.xbuf = p->m2.xbuf;
+  PAT_TRY_CUDA(cudaMemsetAsync(p->m2.xbuf, 0xff, p->m2.xbuf_bytes, st));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
+  PAT_TRY_CUDA(persist2d_launch2(p->R, false, p->varc, a, p->ntiles, st));
+  PAT_TRY_CUDA(persist2d_split_combine(p->d_part, p->d_split_sensor, p->nsplit, p->nt, y0, st));
+  PAT_TRY_CUDA(persist2d_split_combine(p->m2.part, p->d_split_sensor, p->nsplit, p->nt, y1, st));
+  if (p->prof_on) {
+    PAT_TRY(prof_mark(p, st));
+    p->prof_kernels += 1 + (p->nsplit > 0 ? 2 : 0);
+    p->prof_points += 2 * p->N * (long long)(p->nt - 1);
+  }
+  return PAT_OK;
+}
+
+// K* on two right-hand sides.
+static pat_status wave_adjoint2(pat_plan* p, const float* y0, const float* y1, float* x0, float* x1,
+                                cudaStream_t st) {
+  if (!two_field(p)) {
+    PAT_TRY(wave_adjoint(p, y0, x0, st));
+    return wave_adjoint(p, y1, x1, st);
+  }
+  if (p->prof_on) PAT_TRY(prof_mark(p, st));
+  Persist2DArgs a = persist_args(p);
+  a.in = y0;
+  a.out = x0;
+  a.in1 = y1;
+  a.out1 = x1;
+  a.xbuf = p->m2.xbuf;
+  PAT_TRY_CUDA(cudaMemsetAsync(p->m2.xbuf, 0xff, p->m2.xbuf_bytes, st));
+  PAT_TRY_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), st));
+  PAT_TRY_CUDA(persist2d_launch2(p->R, true, p->varc, a, p->ntiles, st));
+  if (p->prof_on) {
+    PAT_TRY(prof_mark(p, st));
+    p->prof_kernels += 1;
+    p->prof_points += 2 * p->N * (long long)(p->nt - 1);
+  }
+  return PAT_OK;
+}
+
+// Two CG solves of the same plan in lockstep (paper Eq. linear_minimization, the coefficient form of
+// solve_device, u0 = 0): each iteration's K and K* of both run as one two-field launch each.
+static pat_status solve_pair(pat_plan* p, const float* y0, const float* y1, double a0, double a1, double s0,
+                             double s1, int iters, float* x0, float* x1, cudaStream_t st) {
+  struct Cg {
+    float *r, *pp, *q, *img, *u, *ybuf;
+    CgScalars* sc;
+    double* partials;
+    unsigned* counter;
+    double alpha, s;
+  };
+  Cg c[2] = {{p->d_r, p->d_p, p->d_q, p->d_img, p->d_u, p->d_ybuf, p->d_sc, p->d_partials, p->d_counter, a0, s0},
+             {p->m2.r, p->m2.p, p->m2.q, p->m2.img, p->m2.u, p->m2.ybuf, p->m2.sc, p->m2.partials, p->m2.counter, a1,
+              s1}};
+  const long long N = p->N;
+  PAT_TRY(wave_adjoint2(p, y0, y1, c[0].img, c[1].img, st));  // r = b = E_s* K* y
+  for (auto& v : c) {
+    PAT_TRY(apply_EsT(p, v.s, v.img, v.r, st));
+    PAT_TRY_CUDA(cg_init_launch(v.r, v.r, v.pp, v.u, N, true, v.partials, v.counter, v.sc, st));
+    count_kernels(p, 1);
+  }
+  for (int k = 0; k < iters; ++k) {
+    for (auto& v : c) PAT_TRY(apply_Es(p, v.s, v.pp, v.img, st));
+    PAT_TRY(wave_forward2(p, c[0].img, c[1].img, c[0].ybuf, c[1].ybuf, st));
+    PAT_TRY(wave_adjoint2(p, c[0].ybuf, c[1].ybuf, c[0].img, c[1].img, st));
+    for (auto& v : c) {
+      PAT_TRY(apply_EsT(p, v.s, v.img, v.q, st));
+      PAT_TRY_CUDA(cg_pq_launch(v.q, v.pp, v.alpha, N, v.partials, v.counter, v.sc, st));
+      PAT_TRY_CUDA(cg_update_launch(v.u, v.r, v.pp, v.q, N, v.partials, v.counter, v.sc, nullptr, p->d_status, st));
+      PAT_TRY_CUDA(cg_direction_launch(v.pp, v.r, N, v.sc, st));
+      count_kernels(p, 3);
+    }
+  }
+  PAT_TRY(apply_Es(p, s0, c[0].u, x0, st));
+  PAT_TRY(apply_Es(p, s1, c[1].u, x1, st));
+  return PAT_OK;
+}
+
+pat_status solve_multi_device(pat_plan* p, int nrhs, const float* const* ys, const double* alphas, const double* ss,
+                              int iters, float* const* xs, cudaStream_t st) {
+  if (nrhs >= 2) PAT_TRY(multi_setup(p, st));
+  int r = 0;
+  for (; r + 1 < nrhs; r += 2)
+    PAT_TRY(solve_pair(p, ys[r], ys[r + 1], alphas[r], alphas[r + 1], ss[r], ss[r + 1], iters, xs[r], xs[r + 1], st));
+  if (r < nrhs) PAT_TRY(solve_device(p, ys[r], alphas[r], ss[r], iters, nullptr, nullptr, xs[r], nullptr, st));
+  return PAT_OK;
+}
+
 // ------------------------------------------------------- host staging
 static bool is_device_ptr(const void* ptr) {
   if (!ptr) return true;
@@ -882,6 +1020,23 @@ pat_status pat_solve_landweber(pat_plan* plan, const float* y, double alpha, dou
   if (x) PAT_TRY(out_back(x, dx, plan->N, hx, st));
   PAT_TRY_CUDA(cudaStreamSynchronize(st));
   return PAT_OK;
+}
+
+pat_status pat_solve_multi(pat_plan* plan, int nrhs, const float* const* ys, const double* alphas,
+                           const double* ss, int iters, float* const* xs, void* stream) {
+  PAT_TRY(check_plan(plan));
+  if (nrhs < 1 || !ys || !alphas || !ss || !xs || iters < 0) {
+    set_error("nrhs >= 1, non-NULL ys / alphas / ss / xs and iters >= 0 required");
+    return PAT_ERR_INVALID;
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    if (!ys[r] || !xs[r] || !is_device_ptr(ys[r]) || !is_device_ptr(xs[r]) || !(alphas[r] > 0.0) ||
+        !std::isfinite(alphas[r]) || !std::isfinite(ss[r])) {
+      set_error("right-hand side %d: ys / xs must be device arrays, alpha finite and > 0, s finite", r);
+      return PAT_ERR_INVALID;
+    }
+  }
+  return solve_multi_device(plan, nrhs, ys, alphas, ss, iters, xs, (cudaStream_t)stream);
 }
 
 pat_status pat_objective(pat_plan* plan, const float* y, double alpha, double s, const float* u, double* J,

@@ -59,7 +59,7 @@ struct pat_plan {
   float* d_sp_a = nullptr;
   float* d_sp_b = nullptr;
   bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
-  int tma3d_zchunk = 0;
+  int tma3d_ctas = 0;  // CTAs of a 3D TMA step launch (one wave, equal shares of the work)
   bool tma2d = false;  // 2D steps through the TMA tile-pipeline kernel (where it applies)
   int* d_tinj3_ptr = nullptr;       // 3D TMA kernel: injection lists per CTA (64 x 16 columns x z chunk)
   pat::InjCell* d_tinj3 = nullptr;  // .local = linear cell index
@@ -84,6 +84,18 @@ struct pat_plan {
   // ---- solver workspace
   float *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_img = nullptr, *d_u = nullptr, *d_ybuf = nullptr;
   pat::CgScalars* d_sc = nullptr;
+  // second right-hand side of pat_solve_multi (allocated on first use): CG vectors, data and image
+  // buffers, split-sensor parts and the two-field exchange strips
+  struct Rhs2 {
+    float *r = nullptr, *p = nullptr, *q = nullptr, *img = nullptr, *u = nullptr, *ybuf = nullptr, *part = nullptr;
+    pat::CgScalars* sc = nullptr;
+    double* partials = nullptr;
+    unsigned* counter = nullptr;
+    void* xbuf = nullptr;
+    size_t xbuf_bytes = 0;
+    bool ready = false;
+    bool two_field = false;  // the two-field persistent kernel fits (both directions)
+  } m2;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   int* d_status = nullptr;
@@ -125,6 +137,9 @@ pat_status fourier_apply(pat_plan* p, double s, const float* in, float* out, cud
 // J(u) = 1/2 ||K E_s u - y||^2 + alpha/2 ||u||^2 into *J (host) and, if grad, its gradient (device, N).
 pat_status objective_device(pat_plan* p, const float* y, double alpha, double s, const float* u, double* J,
                             float* grad, cudaStream_t st);
+// CG of nrhs problems on one plan (own data, alpha, s), two at a time per wave launch on the persistent engine.
+pat_status solve_multi_device(pat_plan* p, int nrhs, const float* const* ys, const double* alphas, const double* ss,
+                              int iters, float* const* xs, cudaStream_t st);
 pat_status landweber_device(pat_plan* p, const float* y, double alpha, double s, int iters, double omega, float* u,
                             float* x, double* J, cudaStream_t st);
 pat_status gmres_device(pat_plan* p, const float* y, double alpha, double s, int iters, float* x, double* res,

@@ -142,46 +142,67 @@ __device__ __forceinline__ void store_state(float* Sn, u64* X, const float V[2][
   }
 }
 
-// Copy the halo of state `step` from the neighbour's strips X into the shared
-// buffers at Sc (second field at Sc + SBUF).  Executed by the RCOUNT threads
-// of one region; returns false if the wait ran out.
-template <int R, bool ADJ>
-__device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsigned step, const int* abort,
-                          long long timeout_ns, int poll_ns) {
+// Copy the halo of state `step` of NR fields from the neighbour's strips X[r]
+// into the shared buffers Sc[r] (second field at Sc[r] + SBUF).  Executed by
+// the RCOUNT threads of one region; returns false if the wait ran out.  Each
+// poll first issues the loads of every word still pending (all fields), then
+// checks their tags, so the L2 round trips of one poll overlap instead of
+// following one another.
+template <int R, bool ADJ, int NR>
+__device__ bool load_halo(float* const (&Sc)[NR], const u64* const (&X)[NR], int region, int rrank, unsigned step,
+                          const int* abort, long long timeout_ns, int poll_ns) {
   using G = Geo<R, ADJ>;
+  constexpr int PMAX = G::PER_NS > G::PER_WE ? G::PER_NS : G::PER_WE;
+  static_assert(NR * PMAX <= 32, "pending bits");
   const bool ns = region < 2;
   const int per = ns ? G::PER_NS : G::PER_WE;
   const int count = ns ? G::NPAIR : G::NSIDE;
-  unsigned pending = 0;
-  for (int j = 0; j < per; ++j)
-    if (rrank + j * RCOUNT < count) pending |= 1u << j;
+  unsigned pending = 0;  // bit r * PMAX + j
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j)
+      if (j < per && rrank + j * RCOUNT < count) pending |= 1u << (r * PMAX + j);
   unsigned long long t0 = 0;
   for (unsigned it = 0; it < (1u << 28); ++it) {
-    for (int j = 0; j < per; ++j) {
-      const unsigned bit = 1u << j;
-      if (!(pending & bit)) continue;
-      const int i = rrank + j * RCOUNT;
-      if (ns) {
-        u64 a, b;
-        ld_word2(X + (region == 0 ? R * TX : 0) + 2 * i, a, b);
-        if (tag_ok<ADJ>(a, step) && tag_ok<ADJ>(b, step)) {
-          const int row = (2 * i) / TX, col = (2 * i) % TX;
-          const int o = (region == 0 ? row : TY + R + row) * PITCH + XOFF + col;
-          *reinterpret_cast<float2*>(Sc + o) = make_float2(word_hi(a), word_hi(b));
-          if (ADJ) *reinterpret_cast<float2*>(Sc + G::SBUF + o) = make_float2(word_lo(a), word_lo(b));
-          pending &= ~bit;
-        }
-      } else {
-        const u64 a = ld_word(X + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
-        if (tag_ok<ADJ>(a, step)) {
-          const int row = i / R, jj = i % R;
-          const int o = (row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj);
-          Sc[o] = word_hi(a);
-          if (ADJ) Sc[G::SBUF + o] = word_lo(a);
-          pending &= ~bit;
+    u64 wa[NR][PMAX], wb[NR][PMAX];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < PMAX; ++j) {
+        wa[r][j] = wb[r][j] = 0ull;
+        if (!(pending & (1u << (r * PMAX + j)))) continue;
+        const int i = rrank + j * RCOUNT;
+        if (ns)
+          ld_word2(X[r] + (region == 0 ? R * TX : 0) + 2 * i, wa[r][j], wb[r][j]);
+        else
+          wa[r][j] = ld_word(X[r] + 2 * R * TX + (region == 2 ? TY * R : 0) + i);
+      }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < PMAX; ++j) {
+        const unsigned bit = 1u << (r * PMAX + j);
+        if (!(pending & bit)) continue;
+        const int i = rrank + j * RCOUNT;
+        if (ns) {
+          if (tag_ok<ADJ>(wa[r][j], step) && tag_ok<ADJ>(wb[r][j], step)) {
+            const int row = (2 * i) / TX, col = (2 * i) % TX;
+            const int o = (region == 0 ? row : TY + R + row) * PITCH + XOFF + col;
+            *reinterpret_cast<float2*>(Sc[r] + o) = make_float2(word_hi(wa[r][j]), word_hi(wb[r][j]));
+            if (ADJ) *reinterpret_cast<float2*>(Sc[r] + G::SBUF + o) = make_float2(word_lo(wa[r][j]), word_lo(wb[r][j]));
+            pending &= ~bit;
+          }
+        } else {
+          if (tag_ok<ADJ>(wa[r][j], step)) {
+            const int row = i / R, jj = i % R;
+            const int o = (row + R) * PITCH + (region == 2 ? XOFF - R + jj : XOFF + TX + jj);
+            Sc[r][o] = word_hi(wa[r][j]);
+            if (ADJ) Sc[r][G::SBUF + o] = word_lo(wa[r][j]);
+            pending &= ~bit;
+          }
         }
       }
-    }
     if (__all_sync(0xffffffffu, pending == 0)) return true;
     if (it == 0) t0 = global_timer_ns();
     if (poll_ns > 0) __nanosleep(poll_ns);
@@ -197,12 +218,17 @@ __device__ bool load_halo(float* Sc, const u64* X, int region, int rrank, unsign
 //   forward  D' = a D + b inc (first step D' = (a-1) P + b inc), P' = P + D'
 //   adjoint  G' = G + inc, Q' = a Q + b G', i.e. Z' = a Z + b kappa G' (final x = ... + ((a-1)/b) Q);
 //   inside the layer Z_lo is only damped (the fields are being damped there).
-template <int R, bool ADJ, bool VARC, bool SP>
+// NR right-hand sides advance together (NR = 2: two independent fields of the same plan, e.g. two CG
+// solves of one medium): every step exchanges both fields' strips in the same round trip and runs both
+// updates between the same barriers.  Inputs / outputs of field r are a.in / a.out (r = 0) and a.in1 /
+// a.out1 (r = 1); field r's exchange words follow field 0's in each slot.
+template <int R, bool ADJ, bool VARC, bool SP, int NR>
 __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persist2DArgs a) {
   using G = Geo<R, ADJ>;
+  static_assert(NR == 1 || !SP, "several right-hand sides run without the absorbing layer");
   extern __shared__ float4 smem4[];
-  float* S0 = reinterpret_cast<float*>(smem4);  // [slot][field] buffers
-  float* J0 = S0 + 2 * G::NF * G::SBUF;         // adjoint injection accumulators, 2 x TY x TX
+  float* S0 = reinterpret_cast<float*>(smem4);   // [slot][rhs][field] buffers
+  float* J0 = S0 + 2 * NR * G::NF * G::SBUF;     // adjoint injection accumulators, [rhs][slot] x TY x TX
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -219,6 +245,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   float2 w2[R + 1];  // stencil weights, packed
 #pragma unroll
   for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
+  const float* IN[2] = {a.in, a.in1};
+  float* OUT[2] = {a.out, a.out1};
+  float* PART[2] = {a.part, a.part1};
 
   // halo duty of this warp: 0 = north, 1 = south, 2 = west, 3 = east neighbour
   const int region = warp & 3;
@@ -229,9 +258,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
   if (region == 2 && tix > 0) nb = tile - 1;
   if (region == 3 && tix < a.tiles_x - 1) nb = tile + 1;
 
-  // forward: P, D ; adjoint: Z (in P, with Z_lo in Pl), G (in D)
-  float P[2][4], D[2][4], K[2][4];
-  float Pl[2][4], Kl[2][4];
+  // forward: P, D ; adjoint: Z (in P, with Z_lo in Pl), G (in D); per right-hand side
+  float P[NR][2][4], D[NR][2][4], Pl[NR][2][4];
+  float K[2][4], Kl[2][4];
   float SA[2][4], SB[2][4];  // layer factors (SP only)
   bool valid[2][4];
 #pragma unroll
@@ -244,40 +273,53 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       const long long gi = (long long)gy * nx + gx;
       K[rr][j] = v ? (VARC ? a.kappa[gi] : a.kappa0) : 0.f;
       Kl[rr][j] = v ? (VARC ? a.kappa_lo[gi] : a.kappa0_lo) : 0.f;
-      P[rr][j] = (!ADJ && v) ? a.in[gi] : 0.f;
       SA[rr][j] = (SP && v) ? a.sp_a[gi] : 1.f;
       SB[rr][j] = (SP && v) ? a.sp_b[gi] : 1.f;
-      D[rr][j] = 0.f;
-      Pl[rr][j] = 0.f;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        P[r][rr][j] = (!ADJ && v) ? IN[r][gi] : 0.f;
+        D[r][rr][j] = 0.f;
+        Pl[r][rr][j] = 0.f;
+      }
     }
-  for (int i = t; i < 2 * G::NF * G::SBUF; i += NTHREADS) S0[i] = 0.f;
+  for (int i = t; i < 2 * NR * G::NF * G::SBUF; i += NTHREADS) S0[i] = 0.f;
   if (ADJ)
-    for (int i = t; i < 2 * TX * TY; i += NTHREADS) J0[i] = 0.f;
+    for (int i = t; i < NR * 2 * TX * TY; i += NTHREADS) J0[i] = 0.f;
   if (t == 0) s_abort = 0;
   __syncthreads();
 
-  {  // publish state 0 (forward: x; adjoint: zero)
-    store_state<R, ADJ>(S0, xbuf + (size_t)tile * 2 * G::SLOT, P, Pl, r0, c0, 0u);
-  }
+  auto Sbuf = [&](int slot, int r) { return S0 + (slot * NR + r) * G::NF * G::SBUF; };
+  auto Jbuf = [&](int r, int slot) { return J0 + (r * 2 + slot) * TX * TY; };
+  auto Xslot = [&](int tl, int slot, int r) { return xbuf + ((size_t)tl * 2 + slot) * NR * G::SLOT + r * G::SLOT; };
+#pragma unroll
+  for (int r = 0; r < NR; ++r)  // publish state 0 (forward: x; adjoint: zero)
+    store_state<R, ADJ>(Sbuf(0, r), Xslot(tile, 0, r), P[r], Pl[r], r0, c0, 0u);
 
   for (int k = 0; k < nt; ++k) {
-    float* Sc = S0 + (k & 1) * G::NF * G::SBUF;
-    float* Jc = J0 + (k & 1) * TX * TY;
     if (ADJ) {  // S^T r_n for this tile's injected cells, n = nt-1-k (independent of the halo: these
                 //  dependent loads overlap the neighbours' exchange)
       const int n = nt - 1 - k;
       const int e1 = a.tile_inj_ptr[tile + 1];
       for (int e = a.tile_inj_ptr[tile] + t; e < e1; e += NTHREADS) {
         const InjCell ic = a.inj[e];
-        float s = 0.f;
-        for (int q = ic.beg; q < ic.end; ++q) s = fmaf(a.ent_w[q], a.in[(long long)a.ent_sensor[q] * nt + n], s);
-        Jc[ic.local] = s;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          float s = 0.f;
+          for (int q = ic.beg; q < ic.end; ++q) s = fmaf(a.ent_w[q], IN[r][(long long)a.ent_sensor[q] * nt + n], s);
+          Jbuf(r, k & 1)[ic.local] = s;
+        }
       }
     }
     // ---- halo of state k from the neighbour's slot (k & 1)
     if (nb >= 0) {
-      const u64* X = xbuf + ((size_t)nb * 2 + (k & 1)) * G::SLOT;
-      if (!load_halo<R, ADJ>(Sc, X, region, rrank, (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
+      float* sc[NR];
+      const u64* xs[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        sc[r] = Sbuf(k & 1, r);
+        xs[r] = Xslot(nb, k & 1, r);
+      }
+      if (!load_halo<R, ADJ, NR>(sc, xs, region, rrank, (unsigned)k, a.abort, a.timeout_ns, a.poll_ns)) {
         if (lane == 0) {
           s_abort = 1;
           atomicCAS(a.status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
@@ -292,84 +334,93 @@ __global__ void __launch_bounds__(NTHREADS, 1) wave2d_persist_kernel(const Persi
       const int e1 = a.tile_samp_ptr[tile + 1];
       for (int e = a.tile_samp_ptr[tile] + t; e < e1; e += NTHREADS) {
         const SampEntry se = a.samp[e];
-        const float* b = Sc + (se.ly + R) * PITCH + XOFF + se.lx;
-        if (se.part < 0) {
-          const float v = se.w[0] * b[0] + se.w[1] * b[1] + se.w[2] * b[PITCH] + se.w[3] * b[PITCH + 1];
-          a.out[(long long)se.sensor * nt + k] = v;
-        } else {
-          a.part[(long long)se.part * nt + k] = se.w[0] * b[0];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const float* b = Sbuf(k & 1, r) + (se.ly + R) * PITCH + XOFF + se.lx;
+          if (se.part < 0) {
+            const float v = se.w[0] * b[0] + se.w[1] * b[1] + se.w[2] * b[PITCH] + se.w[3] * b[PITCH + 1];
+            OUT[r][(long long)se.sensor * nt + k] = v;
+          } else {
+            PART[r][(long long)se.part * nt + k] = se.w[0] * b[0];
+          }
         }
       }
     }
 
-    float L[2][4];
-    lap_2x4_p<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, w2, L);
-    if (ADJ) lap_2x4_p<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, w2, L);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float* Sc = Sbuf(k & 1, r);
+      const float* Jc = Jbuf(r, k & 1);
+      float L[2][4];
+      lap_2x4_p<R, true, false>(Sc, PITCH, r0 + R, XOFF + c0, w2, L);
+      if (ADJ) lap_2x4_p<R, false, true>(Sc + G::SBUF, PITCH, r0 + R, XOFF + c0, w2, L);
 
-    if (k == nt - 1) {
-      if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L Z^1
+      if (k == nt - 1) {
+        if (ADJ) {  // x = S^T r_0 + G^1 + 1/2 L Z^1
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (!valid[rr][j]) continue;
+              const int lr = r0 + rr, lc = c0 + j;
+              float xv = Jc[lr * TX + lc] + D[r][rr][j] + 0.5f * L[rr][j];
+              if (SP && SA[rr][j] != 1.f)  // + ((a-1)/b) Q,  Q = (Z + Z_lo) / kappa
+                xv = fmaf((SA[rr][j] - 1.f) / SB[rr][j], (P[r][rr][j] + Pl[r][rr][j]) / (K[rr][j] + Kl[rr][j]), xv);
+              OUT[r][(long long)(gy0 + lr) * nx + gx0 + lc] = xv;
+            }
+        }
+        continue;
+      }
+
+      float V[2][4], Vl[2][4];
+      if (!ADJ) {
+        const float cf = (k == 0) ? 0.5f : 1.0f;
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (!valid[rr][j]) continue;
-            const int lr = r0 + rr, lc = c0 + j;
-            float xv = Jc[lr * TX + lc] + D[rr][j] + 0.5f * L[rr][j];
-            if (SP && SA[rr][j] != 1.f)  // + ((a-1)/b) Q,  Q = (Z + Z_lo) / kappa
-              xv = fmaf((SA[rr][j] - 1.f) / SB[rr][j], (P[rr][j] + Pl[rr][j]) / (K[rr][j] + Kl[rr][j]), xv);
-            a.out[(long long)(gy0 + lr) * nx + gx0 + lc] = xv;
+            // D += cf (kappa_hi + kappa_lo) L, the product rounded once before it meets D
+            const float inc = fmaf(cf * K[rr][j], L[rr][j], (cf * Kl[rr][j]) * L[rr][j]);
+            if (SP)
+              D[r][rr][j] = k == 0 ? fmaf(SA[rr][j] - 1.f, P[r][rr][j], SB[rr][j] * inc)
+                                   : fmaf(SA[rr][j], D[r][rr][j], SB[rr][j] * inc);
+            else
+              D[r][rr][j] += inc;
+            P[r][rr][j] += D[r][rr][j];
+            V[rr][j] = P[r][rr][j];
+            Vl[rr][j] = 0.f;
+          }
+      } else {
+        float* Jw = Jbuf(r, k & 1);
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int li = (r0 + rr) * TX + c0 + j;
+            const float inc = Jw[li] + L[rr][j];
+            Jw[li] = 0.f;
+            float g = D[r][rr][j] + inc;                         // G += S^T r + L Z
+            const float u = fmaf(K[rr][j], g, Kl[rr][j] * g);    // (kappa_hi + kappa_lo) G, rounded once
+            float z, zl;
+            if (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) {  // Z = a Z + b kappa G inside the layer
+              z = fmaf(SA[rr][j], P[r][rr][j], SB[rr][j] * u);
+              zl = SA[rr][j] * Pl[r][rr][j];
+            } else {
+              float e;
+              z = two_sum(P[r][rr][j], u, e);  // Z += kappa G (compensated)
+              zl = Pl[r][rr][j] + e;
+            }
+            if (!valid[rr][j]) g = z = zl = 0.f;
+            D[r][rr][j] = g;
+            P[r][rr][j] = z;
+            Pl[r][rr][j] = zl;
+            V[rr][j] = z;
+            Vl[rr][j] = zl;
           }
       }
-      break;
+      store_state<R, ADJ>(Sbuf((k + 1) & 1, r), Xslot(tile, (k + 1) & 1, r), V, Vl, r0, c0, (unsigned)(k + 1));
     }
-
-    float V[2][4], Vl[2][4];
-    if (!ADJ) {
-      const float cf = (k == 0) ? 0.5f : 1.0f;
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // D += cf (kappa_hi + kappa_lo) L, the product rounded once before it meets D
-          const float inc = fmaf(cf * K[rr][j], L[rr][j], (cf * Kl[rr][j]) * L[rr][j]);
-          if (SP)
-            D[rr][j] = k == 0 ? fmaf(SA[rr][j] - 1.f, P[rr][j], SB[rr][j] * inc)
-                              : fmaf(SA[rr][j], D[rr][j], SB[rr][j] * inc);
-          else
-            D[rr][j] += inc;
-          P[rr][j] += D[rr][j];
-          V[rr][j] = P[rr][j];
-          Vl[rr][j] = 0.f;
-        }
-    } else {
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int li = (r0 + rr) * TX + c0 + j;
-          const float inc = Jc[li] + L[rr][j];
-          Jc[li] = 0.f;
-          float g = D[rr][j] + inc;                            // G += S^T r + L Z
-          const float u = fmaf(K[rr][j], g, Kl[rr][j] * g);    // (kappa_hi + kappa_lo) G, rounded once
-          float z, zl;
-          if (SP && (SA[rr][j] != 1.f || SB[rr][j] != 1.f)) {  // Z = a Z + b kappa G inside the layer
-            z = fmaf(SA[rr][j], P[rr][j], SB[rr][j] * u);
-            zl = SA[rr][j] * Pl[rr][j];
-          } else {
-            float e;
-            z = two_sum(P[rr][j], u, e);  // Z += kappa G (compensated)
-            zl = Pl[rr][j] + e;
-          }
-          if (!valid[rr][j]) g = z = zl = 0.f;
-          D[rr][j] = g;
-          P[rr][j] = z;
-          Pl[rr][j] = zl;
-          V[rr][j] = z;
-          Vl[rr][j] = zl;
-        }
-    }
-    float* Sn = S0 + ((k + 1) & 1) * G::NF * G::SBUF;
-    store_state<R, ADJ>(Sn, xbuf + ((size_t)tile * 2 + ((k + 1) & 1)) * G::SLOT, V, Vl, r0, c0, (unsigned)(k + 1));
+    if (k == nt - 1) break;
   }
 
 }
@@ -383,9 +434,9 @@ __global__ void split_combine_kernel(const float* __restrict__ part, const int* 
   y[(long long)split_sensor[q] * nt + t] = ((p[0] + p[nt]) + p[2 * nt]) + p[3 * nt];
 }
 
-template <int R, bool ADJ, bool VARC, bool SP>
+template <int R, bool ADJ, bool VARC, bool SP, int NR = 1>
 void* kfn() {
-  return (void*)wave2d_persist_kernel<R, ADJ, VARC, SP>;
+  return (void*)wave2d_persist_kernel<R, ADJ, VARC, SP, NR>;
 }
 
 template <bool SP>
@@ -405,14 +456,29 @@ void* pick_sp(int R, bool adj, bool varc) {
 
 void* pick(int R, bool adj, bool varc) { return pick_sp<false>(R, adj, varc); }
 
-size_t smem_bytes(int R, bool adj) {
-  const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
-  const size_t nf = adj ? 2 : 1;
-  return (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float);
+// two right-hand sides, no absorbing layer
+void* pick2(int R, bool adj, bool varc) {
+#define PAT_P2D2(RR)                                                                              \
+  if (R == RR) {                                                                                  \
+    if (adj) return varc ? kfn<RR, true, true, false, 2>() : kfn<RR, true, false, false, 2>();    \
+    return varc ? kfn<RR, false, true, false, 2>() : kfn<RR, false, false, false, 2>();           \
+  }
+  PAT_P2D2(1)
+  PAT_P2D2(3)
+  PAT_P2D2(5)
+  PAT_P2D2(7)
+#undef PAT_P2D2
+  return nullptr;
 }
 
-cudaError_t prepare(void* f, int R, bool adj) {
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(R, adj));
+size_t smem_bytes(int R, bool adj, int nr = 1) {
+  const size_t sbuf = (size_t)(TY + 2 * R) * PITCH;
+  const size_t nf = adj ? 2 : 1;
+  return (size_t)nr * (2 * nf * sbuf + (adj ? 2 * (size_t)TX * TY : 0)) * sizeof(float);
+}
+
+cudaError_t prepare(void* f, int R, bool adj, int nr = 1) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(R, adj, nr));
 }
 
 }  // namespace
@@ -429,7 +495,7 @@ bool persist2d_supported(int R, bool) { return R == 1 || R == 3 || R == 5 || R =
 int persist2d_tile_x() { return TX; }
 int persist2d_tile_y() { return TY; }
 size_t persist2d_smem_bytes(int R, bool adj) { return smem_bytes(R, adj); }
-size_t persist2d_xbuf_words(int R, bool, int ntiles) { return (size_t)ntiles * 2 * 2 * R * (TX + TY); }
+size_t persist2d_xbuf_words(int R, bool, int ntiles, int nr) { return (size_t)nr * ntiles * 2 * 2 * R * (TX + TY); }
 
 int persist2d_max_ctas(int R, bool adj, bool varc) {
   void* f = pick(R, adj, varc);
@@ -456,6 +522,32 @@ cudaError_t persist2d_launch_layer(int R, bool adj, bool varc, const Persist2DAr
   if (per_sm * sms < nctas) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {(void*)&a};
   return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj), st);
+}
+
+int persist2d_max_ctas2(int R, bool adj, bool varc) {
+  void* f = pick2(R, adj, varc);
+  if (!f) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (prepare(f, R, adj, 2) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NTHREADS, smem_bytes(R, adj, 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per_sm;
+}
+
+cudaError_t persist2d_launch2(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {
+  void* f = pick2(R, adj, varc);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = prepare(f, R, adj, 2);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(f, dim3(nctas), dim3(NTHREADS), args, smem_bytes(R, adj, 2), st);
 }
 
 cudaError_t persist2d_launch(int R, bool adj, bool varc, const Persist2DArgs& a, int nctas, cudaStream_t st) {

@@ -7,8 +7,8 @@
 // kappa L P^n and, because kappa is constant, the adjoint
 // Q^n = 2Q^{n+1} - Q^{n+2} + kappa L Q^{n+1} have the same form).
 //
-// A CTA owns a 64 x 16 column of cells and marches through a chunk of z
-// planes.  One thread issues TMA loads of each plane of `cur` as an
+// A CTA owns a 64 x 16 column of cells and marches through a run of z
+// planes (one wave of CTAs sharing the (column, plane) work evenly).  One thread issues TMA loads of each plane of `cur` as an
 // (64+16) x (16+2R) box (x/y halo included, zero outside the grid) into a
 // ring of shared-memory slots, PD planes ahead of the plane being computed,
 // plus the own 64 x 16 tile of `prev`; completion is tracked by one mbarrier
@@ -51,9 +51,14 @@ __device__ __forceinline__ void fused_sample3(const StepArgs& a, long long gtid)
 }
 
 // INJ: the adjoint's injection S^T r_m into the CTA's own cells of `next` after the step (per-CTA lists)
+// Work split: the grid is one wave of co-resident CTAs; CTA b takes the contiguous share
+// [b W / G, (b+1) W / G) of the W = columns x nz (column, plane) units, z fastest, and marches
+// through it as runs of consecutive planes of one column (a share that crosses into the next column
+// makes a second run with its own z halo).  Every CTA has the same amount of work and no second
+// wave leaves SMs idle at the end of a step.
 template <int R, bool INJ>
 __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mcur,
-                                                             const __grid_constant__ CUtensorMap mprev, int zchunk,
+                                                             const __grid_constant__ CUtensorMap mprev, int cols_x,
                                                              int* status, long long timeout_ns) {
   using G = G3<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -63,17 +68,14 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
   uint64_t* pbars = bars + G::NS;
 
   const int t = threadIdx.x;
-  const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const long long bid = blockIdx.x;
   fused_sample3(a, bid * THREADS + t);
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = (long long)nx * ny;
   const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * 2;
-  const int gx0 = blockIdx.x * TX, gy0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, nz);
-  const int nloc = z1 - z0;         // planes computed
-  const int ncur = nloc + R;        // cur planes j = 0 .. ncur-1 (z = z0 + j) go through the ring
+  const long long W = (long long)cols_x * ((ny + TY - 1) / TY) * nz;
+  const long long w_end = W * (bid + 1) / gridDim.x;
   const bool has_prev = a.prev != nullptr;
   const float ck = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
   const float2 ck2 = dup2(ck), ckl2 = dup2(ckl), ccur2 = dup2(a.c_cur), ncprev2 = dup2(-a.c_prev), m2 = dup2(-2.f);
@@ -81,20 +83,38 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
 #pragma unroll
   for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
 
+  bool ok_all = true;
+  int issued = 0;       // cur planes issued in the current run (thread 0)
+  int issued_prev = 0;  // prev planes issued in the current run
+  bool first_run = true;
+  for (long long w = W * bid / gridDim.x; w < w_end && ok_all;) {
+  const int col = (int)(w / nz);
+  const int z0 = (int)(w - (long long)col * nz);
+  const int z1 = (int)(w_end - w < (long long)(nz - z0) ? z0 + (w_end - w) : nz);
+  w += z1 - z0;
+  const int gx0 = (col % cols_x) * TX, gy0 = (col / cols_x) * TY;
+  const int nloc = z1 - z0;   // planes computed
+  const int ncur = nloc + R;  // cur planes j = 0 .. ncur-1 (z = z0 + j) go through the ring
+  // every copy of the previous run was waited for and every thread is past its last read of the
+  // slots: the barriers start a fresh phase sequence for this run
+  __syncthreads();
   if (t == 0) {
-    for (int s = 0; s < G::NS + G::NSP; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < G::NS + G::NSP; ++s) {
+      if (!first_run) mbar_inval(&bars[s]);
+      mbar_init(&bars[s], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-
-  int issued = 0;  // cur planes issued (thread 0)
+  first_run = false;
+  issued = 0;
+  issued_prev = 0;
   auto issue_cur = [&](int j) {
     issued = j + 1;
     const int s = j % G::NS;
     mbar_expect_tx(&bars[s], G::PLANE * 4);
     tma_load_3d(ring + s * G::PLANE, &mcur, gx0 - XH, gy0 - R, z0 + j, &bars[s]);
   };
-  int issued_prev = 0;
   auto issue_prev = [&](int j) {
     issued_prev = j + 1;
     const int s = j % G::NSP;
@@ -127,7 +147,6 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
       q[R + i][rr] = *reinterpret_cast<const float4*>(ring + (i % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
   }
 
-  bool ok_all = true;
   for (int i = 0; i < nloc; ++i) {
     if (t == 0) {
       fence_proxy_async_shared();  // the slots refilled below were last read through the generic proxy
@@ -182,6 +201,7 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
     }
     __syncthreads();  // the centre slot is refilled by the next iteration's TMA
   }
+  }  // runs
   if (INJ && ok_all) {  // every thread's stores to `next` precede the injection (same CTA)
     __syncthreads();
     for (int e = a.inj_tile_ptr[bid] + t; e < a.inj_tile_ptr[bid + 1]; e += THREADS) {
@@ -202,28 +222,50 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
 }
 
 template <int R, bool INJ>
-cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int zchunk, int* status,
-                     long long timeout_ns, cudaStream_t st) {
-  const size_t smem = G3<R>::SMEM;
+cudaError_t prepare_r() {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)G3<R>::SMEM);
   });
+  return attr_err;
+}
+
+template <int R, bool INJ>
+cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int nctas, int* status,
+                     long long timeout_ns, cudaStream_t st) {
+  const cudaError_t attr_err = prepare_r<R, INJ>();
   if (attr_err != cudaSuccess) return attr_err;
-  dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
-  step3d_tma_kernel<R, INJ><<<grid, THREADS, smem, st>>>(a, mc, mp, zchunk, status, timeout_ns);
+  step3d_tma_kernel<R, INJ><<<nctas, THREADS, G3<R>::SMEM, st>>>(a, mc, mp, (a.nx + TX - 1) / TX, status,
+                                                                  timeout_ns);
   return cudaGetLastError();
 }
 
+// Co-resident CTAs of the step kernel (both variants) on the current device.
+template <int R>
+int resident_r() {
+  int dev = 0, sms = 0, pf = 0, pi = 0;
+  if (prepare_r<R, false>() != cudaSuccess || prepare_r<R, true>() != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, step3d_tma_kernel<R, false>, THREADS, G3<R>::SMEM) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pi, step3d_tma_kernel<R, true>, THREADS, G3<R>::SMEM) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * (pf < pi ? pf : pi);
+}
+
 template <bool INJ>
-cudaError_t launch_i(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+cudaError_t launch_i(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
                      int* status, long long timeout_ns, cudaStream_t st) {
   switch (R) {
-    case 1: return launch_r<1, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 3: return launch_r<3, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 5: return launch_r<5, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
-    case 7: return launch_r<7, INJ>(a, cur, prev, zchunk, status, timeout_ns, st);
+    case 1: return launch_r<1, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
+    case 3: return launch_r<3, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
+    case 5: return launch_r<5, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
+    case 7: return launch_r<7, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -268,27 +310,37 @@ cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUten
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int tma3d_zchunk(int nx, int ny, int nz) {
-  int dev = 0, sms = 148;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long cols = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-  // chunks of at least 16 planes, doubled while the grid keeps >= 6 CTAs per SM (4 are
-  // co-resident: the CTAs of the second wave even out the SMs that received one CTA more
-  // than the others in the first; measured at 256^3: 41.4 us per step with 16-plane chunks
-  // and 1024 CTAs, 43.0 with 32-plane chunks and 512 CTAs)
-  int zc = 16;
-  while (zc < nz && cols * ((nz + zc * 2 - 1) / (zc * 2)) >= 6LL * sms) zc *= 2;
-  return zc;
+// CTAs of a step launch: one wave of co-resident CTAs, at most one per (column, plane) unit.
+int tma3d_ctas(int R, int nx, int ny, int nz) {
+  int cap = 0;
+  switch (R) {
+    case 1: cap = resident_r<1>(); break;
+    case 3: cap = resident_r<3>(); break;
+    case 5: cap = resident_r<5>(); break;
+    case 7: cap = resident_r<7>(); break;
+    default: return 0;
+  }
+  const long long units = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz;
+  return (int)(units < cap ? units : cap);
 }
 
-long long tma3d_threads(int nx, int ny, int nz, int zchunk) {
-  return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk) * THREADS;
+// CTA of a launch of `nctas` CTAs whose share holds cell (x, y, z) (the kernel's work split).
+int tma3d_cta_of(int nx, int ny, int nz, int nctas, int x, int y, int z) {
+  const long long cols_x = (nx + TX - 1) / TX;
+  const long long W = cols_x * ((ny + TY - 1) / TY) * nz;
+  const long long w = ((long long)(y / TY) * cols_x + x / TX) * nz + z;
+  long long b = w * nctas / W;
+  while (b + 1 < nctas && W * (b + 1) / nctas <= w) ++b;
+  while (b > 0 && W * b / nctas > w) --b;
+  return (int)b;
 }
 
-cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int zchunk,
+long long tma3d_threads(int nctas) { return (long long)nctas * THREADS; }
+
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
                               int* status, long long timeout_ns, cudaStream_t st) {
-  return a.inj_r ? launch_i<true>(R, a, cur, prev, zchunk, status, timeout_ns, st)
-                 : launch_i<false>(R, a, cur, prev, zchunk, status, timeout_ns, st);
+  return a.inj_r ? launch_i<true>(R, a, cur, prev, nctas, status, timeout_ns, st)
+                 : launch_i<false>(R, a, cur, prev, nctas, status, timeout_ns, st);
 }
 
 }  // namespace pat

@@ -130,6 +130,14 @@ class Plan:
         return u, x, (log[:iters] if want_log else None)
 
 
+    def solve_multi(self, ys, alphas, ss, iters, stream=None):
+        """CG for several right-hand sides of this plan (two per wave launch on
+        the persistent engine); returns the images."""
+        ys = [self._f32(y) for y in ys]
+        xs = [torch.empty(self.shape, device="cuda", dtype=torch.float32) for _ in ys]
+        _lib.pat_solve_multi(self.handle, ys, alphas, ss, iters, xs, self._stream(stream))
+        return xs
+
     def solve_gmres(self, y, alpha, s, iters, want_log=False, stream=None):
         """GMRES on the paper's image-space system; returns (x, res, J) with
         res and J numpy arrays of iters+1 values (None unless want_log)."""

@@ -97,3 +97,28 @@ def test_timeout_is_reported_not_hung():
     assert rel(plan.forward(w.x_true).cpu().numpy(), wave.forward(w.x_true)) <= 1e-5
     assert plan.check() == 0
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("varc", [True, False])
+def test_solve_multi_matches_single_solves(varc):
+    """pat_solve_multi: three right-hand sides (a pair in two-field launches
+    of the persistent engine, then one alone) give bit for bit the images of
+    three pat_solve calls, and each is within the solve bound of the oracle's
+    CG with the same data, alpha and s."""
+    torch = need_gpu()
+    w = synth.workload("vessels", n=128, nt=400, levels=4, iters=12) if varc else synth.workload("small", n=96,
+                                                                                                   nt=200, order=8)
+    plan, wave, wav = make_pair(w)
+    assert plan.path == 1
+    rng = np.random.default_rng(31)
+    ys = [synth.add_noise(wave.forward(w.x_true), w.noise, rng) for _ in range(3)]
+    alphas, ss = [3e-3, 1e-2, 2e-2], [1.0, 2.0, 1.5]
+    iters = 8
+    xs = plan.solve_multi(ys, alphas, ss, iters)
+    assert plan.check() == 0
+    for y, a, s, x in zip(ys, alphas, ss, xs):
+        _, x1, _ = plan.solve(y, a, s, iters)
+        assert torch.equal(x, x1)
+        _, x_ref, _ = oracle.cg(wave, wav, y, a, s, iters)
+        assert rel(x.cpu().numpy(), x_ref) <= TOL_X
+
