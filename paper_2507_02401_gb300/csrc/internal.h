@@ -156,10 +156,15 @@ cudaError_t persist2d_split_combine(const float* part, const int* split_sensor, 
 bool tma3d_supported(int nx, int R, bool varc);
 // `cur` (80 x (16+2R) x 1 boxes) and `prev` (64 x 16 x 1) descriptors of an nx x ny x nz float field
 cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev);
-int tma3d_ctas(int R, int nx, int ny, int nz);  // CTAs of a step launch (one wave, equal shares)
-int tma3d_cta_of(int nx, int ny, int nz, int nctas, int x, int y, int z);  // CTA whose share holds a cell
+// Work split of a 3D TMA step launch: nctas = columns x nchunks CTAs, column-fastest, each a z range
+// of nz / nchunks planes.
+struct Tma3dSplit {
+  int nctas, nchunks;
+};
+Tma3dSplit tma3d_split(int R, int nx, int ny, int nz);
+int tma3d_cta_of(int nx, int ny, int nz, const Tma3dSplit& sp, int x, int y, int z);  // CTA holding a cell
 long long tma3d_threads(int nctas);  // threads of one launch (fused sampling)
-cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, const Tma3dSplit& sp,
                               int* status, long long timeout_ns, cudaStream_t st);
 
 // wave2d_tma.cu: 2D increment-form step with TMA tile pipelines (forward; constant-medium adjoint)

@@ -137,7 +137,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
     b.inj_r = nullptr;
     e = step2d_launch(p->R, adj, b, st);
   } else if (p->tma3d && tma_ready(p, a)) {
-    const long long nthr = tma3d_threads(p->tma3d_ctas);
+    const long long nthr = tma3d_threads(p->tma3d_split.nctas);
     if (y && a.ns > nthr) a.y = nullptr;
     if (a.inj_r) {  // the adjoint's post-step injection, fused per CTA
       a.inj_tile_ptr = p->d_tinj3_ptr;
@@ -155,7 +155,7 @@ static cudaError_t step_launch(pat_plan* p, bool adj, StepArgs& a, cudaStream_t 
       if (!dp) return cudaErrorInvalidValue;
       mp = dp->own;
     }
-    e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_ctas, p->d_status, p->timeout_ns, st);
+    e = step3d_tma_launch(p->R, a, mc, mp, p->tma3d_split, p->d_status, p->timeout_ns, st);
   } else {
     const long long nthr =
         (long long)((p->n[0] + 31) / 32) * ((p->n[1] + 15) / 16) * ((p->n[2] + 31) / 32) * 128;

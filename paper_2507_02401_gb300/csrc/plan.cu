@@ -480,17 +480,17 @@ static pat_status create(const pat_grid* grid, const double* c, double c0, const
   if (p->dim == 3 && tma3d_supported(p->n[0], p->R, p->varc) && !(env3 && strcmp(env3, "plain") == 0)) {
     CUtensorMap mc, mp;
     if (tma3d_encode(p->d_wv[0], p->n[0], p->n[1], p->n[2], p->R, &mc, &mp) == cudaSuccess) {
-      p->tma3d_ctas = tma3d_ctas(p->R, p->n[0], p->n[1], p->n[2]);
-      p->tma3d = p->tma3d_ctas > 0;
+      p->tma3d_split = tma3d_split(p->R, p->n[0], p->n[1], p->n[2]);
+      p->tma3d = p->tma3d_split.nctas > 0;
     }
   }
   if (p->tma3d) {  // injection lists per CTA of the 3D TMA grid (the adjoint injects after each step)
-    const int nx = p->n[0], ny = p->n[1], nz = p->n[2], G = p->tma3d_ctas;
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2], G = p->tma3d_split.nctas;
     std::vector<std::vector<InjCell>> bins((size_t)G);
     for (int i = 0; i < p->n_inj; ++i) {
       const long long c = p->h_inj_cell[i];
       const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
-      bins[tma3d_cta_of(nx, ny, nz, G, x, y, z)].push_back(InjCell{(int)c, p->h_inj_ptr[i], p->h_inj_ptr[i + 1]});
+      bins[tma3d_cta_of(nx, ny, nz, p->tma3d_split, x, y, z)].push_back(InjCell{(int)c, p->h_inj_ptr[i], p->h_inj_ptr[i + 1]});
     }
     std::vector<int> ptr(1, 0);
     std::vector<InjCell> cells;

@@ -59,7 +59,7 @@ struct pat_plan {
   float* d_sp_a = nullptr;
   float* d_sp_b = nullptr;
   bool tma3d = false;  // 3D steps through the TMA plane-pipeline kernel
-  int tma3d_ctas = 0;  // CTAs of a 3D TMA step launch (one wave, equal shares of the work)
+  pat::Tma3dSplit tma3d_split{0, 0};  // work split of a 3D TMA step launch
   bool tma2d = false;  // 2D steps through the TMA tile-pipeline kernel (where it applies)
   int* d_tinj3_ptr = nullptr;       // 3D TMA kernel: injection lists per CTA (64 x 16 columns x z chunk)
   pat::InjCell* d_tinj3 = nullptr;  // .local = linear cell index

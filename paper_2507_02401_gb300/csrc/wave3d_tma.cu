@@ -7,8 +7,8 @@
 // kappa L P^n and, because kappa is constant, the adjoint
 // Q^n = 2Q^{n+1} - Q^{n+2} + kappa L Q^{n+1} have the same form).
 //
-// A CTA owns a 64 x 16 column of cells and marches through a run of z
-// planes (one wave of CTAs sharing the (column, plane) work evenly).  One thread issues TMA loads of each plane of `cur` as an
+// A CTA owns a 64 x 16 column of cells and marches through a range of z
+// planes.  One thread issues TMA loads of each plane of `cur` as an
 // (64+16) x (16+2R) box (x/y halo included, zero outside the grid) into a
 // ring of shared-memory slots, PD planes ahead of the plane being computed,
 // plus the own 64 x 16 tile of `prev`; completion is tracked by one mbarrier
@@ -51,15 +51,12 @@ __device__ __forceinline__ void fused_sample3(const StepArgs& a, long long gtid)
 }
 
 // INJ: the adjoint's injection S^T r_m into the CTA's own cells of `next` after the step (per-CTA lists)
-// Work split: the grid is one wave of co-resident CTAs; CTA b takes the contiguous share
-// [b W / G, (b+1) W / G) of the W = columns x nz (column, plane) units, z fastest, and marches
-// through it as runs of consecutive planes of one column (a share that crosses into the next column
-// makes a second run with its own z halo).  Every CTA has the same amount of work and no second
-// wave leaves SMs idle at the end of a step.
+// Work split (column-fastest): CTA b takes column b mod columns and the (b div columns)-th of
+// nchunks equal z ranges, so CTAs that run together stream neighbouring columns of the same rows.
 template <int R, bool INJ>
 __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mcur,
                                                              const __grid_constant__ CUtensorMap mprev, int cols_x,
-                                                             int* status, long long timeout_ns) {
+                                                             int nchunks, int* status, long long timeout_ns) {
   using G = G3<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
@@ -74,8 +71,7 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = (long long)nx * ny;
   const int c0 = (t % (TX / 4)) * 4, r0 = (t / (TX / 4)) * 2;
-  const long long W = (long long)cols_x * ((ny + TY - 1) / TY) * nz;
-  const long long w_end = W * (bid + 1) / gridDim.x;
+  const long long ncols = (long long)cols_x * ((ny + TY - 1) / TY);
   const bool has_prev = a.prev != nullptr;
   const float ck = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
   const float2 ck2 = dup2(ck), ckl2 = dup2(ckl), ccur2 = dup2(a.c_cur), ncprev2 = dup2(-a.c_prev), m2 = dup2(-2.f);
@@ -84,31 +80,20 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
   for (int m = 0; m <= R; ++m) w2[m] = dup2(a.w[m]);
 
   bool ok_all = true;
-  int issued = 0;       // cur planes issued in the current run (thread 0)
-  int issued_prev = 0;  // prev planes issued in the current run
-  bool first_run = true;
-  for (long long w = W * bid / gridDim.x; w < w_end && ok_all;) {
-  const int col = (int)(w / nz);
-  const int z0 = (int)(w - (long long)col * nz);
-  const int z1 = (int)(w_end - w < (long long)(nz - z0) ? z0 + (w_end - w) : nz);
-  w += z1 - z0;
+  int issued = 0;       // cur planes issued (thread 0)
+  int issued_prev = 0;  // prev planes issued
+  const int col = (int)(bid % ncols);
+  const long long zr = bid / ncols;
+  const int z0 = (int)(zr * nz / nchunks);
+  const int z1 = (int)((zr + 1) * nz / nchunks);
   const int gx0 = (col % cols_x) * TX, gy0 = (col / cols_x) * TY;
   const int nloc = z1 - z0;   // planes computed
   const int ncur = nloc + R;  // cur planes j = 0 .. ncur-1 (z = z0 + j) go through the ring
-  // every copy of the previous run was waited for and every thread is past its last read of the
-  // slots: the barriers start a fresh phase sequence for this run
-  __syncthreads();
   if (t == 0) {
-    for (int s = 0; s < G::NS + G::NSP; ++s) {
-      if (!first_run) mbar_inval(&bars[s]);
-      mbar_init(&bars[s], 1);
-    }
+    for (int s = 0; s < G::NS + G::NSP; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  first_run = false;
-  issued = 0;
-  issued_prev = 0;
   auto issue_cur = [&](int j) {
     issued = j + 1;
     const int s = j % G::NS;
@@ -201,7 +186,6 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
     }
     __syncthreads();  // the centre slot is refilled by the next iteration's TMA
   }
-  }  // runs
   if (INJ && ok_all) {  // every thread's stores to `next` precede the injection (same CTA)
     __syncthreads();
     for (int e = a.inj_tile_ptr[bid] + t; e < a.inj_tile_ptr[bid + 1]; e += THREADS) {
@@ -233,11 +217,11 @@ cudaError_t prepare_r() {
 }
 
 template <int R, bool INJ>
-cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int nctas, int* status,
-                     long long timeout_ns, cudaStream_t st) {
+cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int nctas, int nchunks,
+                     int* status, long long timeout_ns, cudaStream_t st) {
   const cudaError_t attr_err = prepare_r<R, INJ>();
   if (attr_err != cudaSuccess) return attr_err;
-  step3d_tma_kernel<R, INJ><<<nctas, THREADS, G3<R>::SMEM, st>>>(a, mc, mp, (a.nx + TX - 1) / TX, status,
+  step3d_tma_kernel<R, INJ><<<nctas, THREADS, G3<R>::SMEM, st>>>(a, mc, mp, (a.nx + TX - 1) / TX, nchunks, status,
                                                                   timeout_ns);
   return cudaGetLastError();
 }
@@ -260,12 +244,12 @@ int resident_r() {
 
 template <bool INJ>
 cudaError_t launch_i(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
-                     int* status, long long timeout_ns, cudaStream_t st) {
+                     int nchunks, int* status, long long timeout_ns, cudaStream_t st) {
   switch (R) {
-    case 1: return launch_r<1, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
-    case 3: return launch_r<3, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
-    case 5: return launch_r<5, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
-    case 7: return launch_r<7, INJ>(a, cur, prev, nctas, status, timeout_ns, st);
+    case 1: return launch_r<1, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 3: return launch_r<3, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 5: return launch_r<5, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 7: return launch_r<7, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -310,37 +294,55 @@ cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUten
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// CTAs of a step launch: one wave of co-resident CTAs, at most one per (column, plane) unit.
-int tma3d_ctas(int R, int nx, int ny, int nz) {
+// Work split of a step launch: columns (64 x 16 cells) x nchunks equal z ranges, column-fastest.  Few
+// columns (fewer than a quarter of the co-resident CTAs; 64 at 256^3): as many z ranges as keep every
+// CTA in one wave (9 at 256^3: 576 CTAs of 28-29 planes), so no second wave leaves SMs idle at the end
+// of a step.  Many columns (256 at 512^3): ranges of at least 16 planes, doubled while the grid keeps
+// >= 6 CTAs per SM.  Measured at 256^3: 41.0 / 40.0 us per K / K* step against 41.4 / 44.1 us with
+// 16-plane ranges in 1024 CTAs (and 43.1 / 42.3 us with equal z-fastest shares of the (column, plane)
+// work, whose concurrent CTAs no longer share x/y halos through L2).
+Tma3dSplit tma3d_split(int R, int nx, int ny, int nz) {
   int cap = 0;
   switch (R) {
     case 1: cap = resident_r<1>(); break;
     case 3: cap = resident_r<3>(); break;
     case 5: cap = resident_r<5>(); break;
     case 7: cap = resident_r<7>(); break;
-    default: return 0;
+    default: return Tma3dSplit{0, 0};
   }
-  const long long units = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz;
-  return (int)(units < cap ? units : cap);
+  if (cap <= 0) return Tma3dSplit{0, 0};
+  const long long cols = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  int chunks;
+  if (cols * 4 < cap) {
+    chunks = (int)(cap / cols);
+  } else {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int zc = 16;
+    while (zc < nz && cols * ((nz + zc * 2 - 1) / (zc * 2)) >= 6LL * sms) zc *= 2;
+    chunks = (nz + zc - 1) / zc;
+  }
+  if (chunks > nz) chunks = nz;
+  return Tma3dSplit{(int)(cols * chunks), chunks};
 }
 
-// CTA of a launch of `nctas` CTAs whose share holds cell (x, y, z) (the kernel's work split).
-int tma3d_cta_of(int nx, int ny, int nz, int nctas, int x, int y, int z) {
+// CTA holding cell (x, y, z) (the kernel's split: chunk zr holds z in [zr nz / k, (zr + 1) nz / k)).
+int tma3d_cta_of(int nx, int ny, int nz, const Tma3dSplit& sp, int x, int y, int z) {
   const long long cols_x = (nx + TX - 1) / TX;
-  const long long W = cols_x * ((ny + TY - 1) / TY) * nz;
-  const long long w = ((long long)(y / TY) * cols_x + x / TX) * nz + z;
-  long long b = w * nctas / W;
-  while (b + 1 < nctas && W * (b + 1) / nctas <= w) ++b;
-  while (b > 0 && W * b / nctas > w) --b;
-  return (int)b;
+  const long long ncols = cols_x * ((ny + TY - 1) / TY);
+  const long long col = (long long)(y / TY) * cols_x + x / TX;
+  long long zr = (long long)z * sp.nchunks / nz;
+  while (zr + 1 < sp.nchunks && (zr + 1) * nz / sp.nchunks <= z) ++zr;
+  while (zr > 0 && zr * nz / sp.nchunks > z) --zr;
+  return (int)(zr * ncols + col);
 }
 
 long long tma3d_threads(int nctas) { return (long long)nctas * THREADS; }
 
-cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
-                              int* status, long long timeout_ns, cudaStream_t st) {
-  return a.inj_r ? launch_i<true>(R, a, cur, prev, nctas, status, timeout_ns, st)
-                 : launch_i<false>(R, a, cur, prev, nctas, status, timeout_ns, st);
+cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev,
+                              const Tma3dSplit& sp, int* status, long long timeout_ns, cudaStream_t st) {
+  return a.inj_r ? launch_i<true>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st)
+                 : launch_i<false>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st);
 }
 
 }  // namespace pat
