@@ -153,17 +153,10 @@ __global__ void __launch_bounds__(S_THREADS) dwt2d_synthesis_kernel(const float*
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ float4 f4fma(float w, const float4& v, const float4& a) {
-  return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
-}
-__device__ __forceinline__ float4 f4scale(float w, const float4& v) {
-  return make_float4(w * v.x, w * v.y, w * v.z, w * v.w);
-}
 
 // Four consecutive values as two packed FP32x2 pairs (FFMA2 / FMUL2: one
 // instruction per pair, each lane rounded as the scalar instruction would).
@@ -196,6 +189,12 @@ struct F4x2 {
 // visible.  Without the launch attribute both instructions are no-ops.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Row stride of a staged 3D window: an odd number of 16-byte units.  The x
+// pass has each thread read 16 bytes every 32 bytes of a row, a warp spanning
+// four rows; with an even stride every row of the warp starts on the same
+// bank and each 16-byte load takes twice the minimum shared-memory wavefronts.
+__host__ __device__ constexpr int pad_row(int w) { return (w / 4) % 2 == 0 ? w + 4 : w; }
 
 // Analysis: tile (kx0, ky0) gives OX x OY coefficients of each band from the
 // input window rows [2 ky0, 2 ky0 + 2 OY + L - 2) x columns [2 kx0, 2 kx0 +
@@ -522,25 +521,23 @@ struct A3F {
   static constexpr int OX = 32, OY = 8, THREADS = 256, NSLOT = 4;
   static constexpr int HX = (L - 2 + 3) / 4 * 4;
   static constexpr int WX = 2 * OX + HX;
+  static constexpr int WXP = pad_row(WX);  // row stride in shared memory
   static constexpr int WY = 2 * OY + L - 2;
   static constexpr int NQ = WX / 4;
-  static constexpr int SLAB_BYTES = NSLOT * WY * WX * 4;  // multiple of 16
+  static constexpr int SLAB_BYTES = NSLOT * WY * WXP * 4;  // multiple of 16
   static constexpr int X_BYTES = WY * OX * 4;
-  static constexpr int SMEM = SLAB_BYTES + 2 * X_BYTES + L * THREADS * 16;
+  static constexpr int SMEM = SLAB_BYTES + 2 * X_BYTES;
 };
 
 template <int L>
-__global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
+__global__ void __launch_bounds__(256, 3) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
                                                                   const Bands8 out, float wdet, const Filt f,
                                                                   int cols_x, int ncols) {
   using G = A3F<L>;
   extern __shared__ __align__(16) unsigned char dsm[];  // G::SMEM bytes (more than the static 48 KB)
-  auto slab = reinterpret_cast<float(*)[G::WY][G::WX]>(dsm);
+  auto slab = reinterpret_cast<float(*)[G::WY][G::WXP]>(dsm);
   auto xl = reinterpret_cast<float(*)[G::OX]>(dsm + G::SLAB_BYTES);
   auto xh = reinterpret_cast<float(*)[G::OX]>(dsm + G::SLAB_BYTES + G::X_BYTES);
-  auto ring = reinterpret_cast<float4(*)[G::THREADS]>(dsm + G::SLAB_BYTES + 2 * G::X_BYTES);  // each thread's
-                                                                                             // quarter values of
-                                                                                             // the last L planes
   const int t = threadIdx.x;
   const int nx2 = nx >> 1, ny2 = ny >> 1, nz2 = nz >> 1;
   griddep_wait();
@@ -578,14 +575,14 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
         const float* src = col0 + (long long)z * ny * nx;
         for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
           const int r = i / G::NQ, q = i - r * G::NQ;
-          cp_async16(dst + r * G::WX + 4 * q, src + (long long)r * nx + 4 * q);
+          cp_async16(dst + r * G::WXP + 4 * q, src + (long long)r * nx + 4 * q);
         }
       } else {
         const long long zoff = (long long)z * ny;
         for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
           const int r = i / G::NQ, q = i - r * G::NQ;
           const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;
-          cp_async16(dst + r * G::WX + 4 * q, in + (zoff + gy) * nx + gx);
+          cp_async16(dst + r * G::WXP + 4 * q, in + (zoff + gy) * nx + gx);
         }
       }
     }
@@ -595,11 +592,12 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
   for (int pl = 0; pl < G::NSLOT - 1; ++pl) load(pl);
   const int oy = ky0 + ky, ox = kx0 + 4 * qx;
   const bool store = oy < ny2 && ox < nx2;
-  for (int pl = 0; pl < nplanes; ++pl) {
+  // x and y passes of input plane pl: this thread's quarter values of the plane
+  auto plane = [&](int pl) -> F4x2 {
     load(pl + G::NSLOT - 1);
     cp_async_wait_group<G::NSLOT - 1>();  // this thread's copies of plane pl have landed
     __syncthreads();                      // ... and every other thread's
-    const float(*w)[G::WX] = slab[pl % G::NSLOT];
+    const float(*w)[G::WXP] = slab[pl % G::NSLOT];
     for (int i = t; i < G::WY * (G::OX / 4); i += G::THREADS) {  // along x
       const int r = i / (G::OX / 4), q = i - r * (G::OX / 4);
       float v[8 + G::HX];
@@ -629,26 +627,34 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_fast_kernel(const float* _
     F4x2 v4;  // along y
 #pragma unroll
     for (int j = 0; j < L; ++j) v4.fma(fy[j], F4x2::ld(&src[2 * ky + j][4 * qx]));
-    ring[pl % L][t] = v4.f4();  // read back only by this thread
-    if (pl >= L - 1 && ((pl - (L - 1)) & 1) == 0) {  // ring holds input planes 2m .. 2m + L - 1: output plane m
-      const int kz = kz0 + ((pl - (L - 1)) >> 1);
-      const int base = pl - (L - 1);  // plane 2m (relative)
-      F4x2 lo, hi;
+    return v4;
+  };
+  // along z in registers: acc[i] accumulates output plane m = k - (NA - 1) + i while the pair of input
+  // planes 2k, 2k + 1 passes (taps 2 (NA - 1 - i) and 2 (NA - 1 - i) + 1, in tap order)
+  constexpr int NA = L / 2;
+  F4x2 alo[NA], ahi[NA];
+  for (int k = 0; 2 * k < nplanes; ++k) {
 #pragma unroll
-      for (int j = 0; j < L; ++j) {
-        const float4 r4 = ring[(base + j) % L][t];
-        F4x2 rv;
-        rv.p0 = make_float2(r4.x, r4.y);
-        rv.p1 = make_float2(r4.z, r4.w);
-        lo.fma(dup2(f.h[j]), rv);
-        hi.fma(dup2(f.g[j]), rv);
-      }
-      if (store) {
-        const long long o = ((long long)kz * ny2 + oy) * nx2 + ox;
-        lo.scale(wlo).st(plo + o);
-        hi.scale(whi).st(phi + o);
+    for (int e = 0; e < 2; ++e) {
+      const F4x2 v = plane(2 * k + e);
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        alo[i].fma(dup2(f.h[2 * (NA - 1 - i) + e]), v);
+        ahi[i].fma(dup2(f.g[2 * (NA - 1 - i) + e]), v);
       }
     }
+    if (k >= NA - 1 && store) {  // output plane kz0 + k - (NA - 1) has all its L taps
+      const long long o = ((long long)(kz0 + k - (NA - 1)) * ny2 + oy) * nx2 + ox;
+      alo[0].scale(wlo).st(plo + o);
+      ahi[0].scale(whi).st(phi + o);
+    }
+#pragma unroll
+    for (int i = 0; i < NA - 1; ++i) {
+      alo[i] = alo[i + 1];
+      ahi[i] = ahi[i + 1];
+    }
+    alo[NA - 1] = F4x2();
+    ahi[NA - 1] = F4x2();
   }
   }  // runs
 }
