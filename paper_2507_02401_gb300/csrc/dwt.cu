@@ -524,6 +524,7 @@ struct A3F {
   static constexpr int WXP = pad_row(WX);  // row stride in shared memory
   static constexpr int WY = 2 * OY + L - 2;
   static constexpr int NQ = WX / 4;
+  static constexpr int NCH = (WY * NQ + THREADS - 1) / THREADS;  // 16-byte chunks per thread and plane
   static constexpr int SLAB_BYTES = NSLOT * WY * WXP * 4;  // multiple of 16
   static constexpr int X_BYTES = WY * OX * 4;
   static constexpr int SMEM = SLAB_BYTES + 2 * X_BYTES;
@@ -564,27 +565,25 @@ __global__ void __launch_bounds__(256, 3) dwt3d_analysis_fast_kernel(const float
   const int kx0 = (colid % cols_x) * G::OX, ky0 = (colid / cols_x) * G::OY;
   __syncthreads();  // the previous run is done with the shared buffers
   const int nplanes = 2 * (kz1 - kz0) + L - 2;  // input planes 2 kz0 .. 2 kz1 + L - 3 (periodic)
-  const bool interior_xy = 2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny;
-  const float* col0 = in + (long long)(2 * ky0) * nx + 2 * kx0;
+  // this thread's 16-byte chunks of a plane's window: shared offset and in-plane source offset (with the
+  // periodic wrap) are the same for every plane of the run, so they are computed once here
+  int soff[G::NCH], goff[G::NCH];
+#pragma unroll
+  for (int c = 0; c < G::NCH; ++c) {
+    const int i = t + c * G::THREADS;
+    const int r = i / G::NQ, q = i - r * G::NQ;
+    soff[c] = i < G::WY * G::NQ ? r * G::WXP + 4 * q : -1;
+    goff[c] = ((2 * ky0 + r) % ny) * nx + (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: a chunk never straddles the wrap
+  }
   auto load = [&](int pl) {
     if (pl < nplanes) {
       int z = 2 * kz0 + pl;
       while (z >= nz) z -= nz;
       float* dst = &slab[pl % G::NSLOT][0][0];
-      if (interior_xy) {
-        const float* src = col0 + (long long)z * ny * nx;
-        for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-          const int r = i / G::NQ, q = i - r * G::NQ;
-          cp_async16(dst + r * G::WXP + 4 * q, src + (long long)r * nx + 4 * q);
-        }
-      } else {
-        const long long zoff = (long long)z * ny;
-        for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-          const int r = i / G::NQ, q = i - r * G::NQ;
-          const int gy = (2 * ky0 + r) % ny, gx = (2 * kx0 + 4 * q) % nx;
-          cp_async16(dst + r * G::WXP + 4 * q, in + (zoff + gy) * nx + gx);
-        }
-      }
+      const float* src = in + (long long)z * ny * nx;
+#pragma unroll
+      for (int c = 0; c < G::NCH; ++c)
+        if (soff[c] >= 0) cp_async16(dst + soff[c], src + goff[c]);
     }
     cp_async_commit();  // one group per plane (possibly empty) keeps the group count uniform
   };
@@ -669,6 +668,7 @@ struct S3F {
   static constexpr int NQ = WX / 4;
   static constexpr int K0 = (CX - LH) & ~1;
   static constexpr int NK2 = (CX + 2 - K0) / 2;
+  static constexpr int NCH = (8 * WY * NQ + THREADS - 1) / THREADS;  // 16-byte chunks per thread and plane
 };
 
 // Synthesis of one 3D level: coefficient extents (nx/2, ny/2, nz/2) -> (nx, ny, nz).
@@ -676,7 +676,7 @@ struct S3F {
 // four zb = 1 bands gives two full-resolution planes P_lo(m), P_hi(m); output
 // plane 2m + e is then sum_jj h_{2jj+e} P_lo(m - jj) + g_{2jj+e} P_hi(m - jj).
 template <int L>
-__global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
+__global__ void __launch_bounds__(256, 3) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
                                                                    int nz, float* __restrict__ out, const Filt f,
                                                                    int cols_x, int ncols) {
   using G = S3F<L>;
@@ -699,17 +699,26 @@ __global__ void __launch_bounds__(256) dwt3d_synthesis_fast_kernel(const CBands8
   const int kx0 = (colid % cols_x) * G::OX, ky0 = (colid / cols_x) * G::OY;
   __syncthreads();  // the previous run is done with the shared buffers
   const int nplanes = kz1 - kz0 + G::LH;  // coefficient planes kz0 - LH .. kz1 - 1 (periodic)
-  const bool interior_xy = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= cx && ky0 + G::OY <= cy;
+  // this thread's 16-byte chunks of a plane's eight band windows: shared offset and source (band, periodic
+  // in-plane position) are the same for every coefficient plane of the run, so they are computed once here
+  int soff[G::NCH];
+  const float* gsrc[G::NCH];
+#pragma unroll
+  for (int c = 0; c < G::NCH; ++c) {
+    const int i = t + c * G::THREADS;
+    const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
+    const int r = rq / G::NQ, q = rq - r * G::NQ;
+    const bool ok = i < 8 * G::WY * G::NQ;
+    soff[c] = ok ? (b * G::WY + r) * G::WX + 4 * q : -1;
+    gsrc[c] = ok ? band_sel(in, b) + pmod(ky0 - G::LH + r, cy) * cx + pmod(kx0 - G::CX + 4 * q, cx) : nullptr;
+  }
   auto load = [&](int pl) {
     if (pl < nplanes) {
-      const long long zoff = (long long)pmod(kz0 - G::LH + pl, cz2) * cy;
-      for (int i = t; i < 8 * G::WY * G::NQ; i += G::THREADS) {
-        const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
-        const int r = rq / G::NQ, q = rq - r * G::NQ;
-        const int ky = interior_xy ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, cy);
-        const int kx = interior_xy ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, cx);
-        cp_async16(&cw[pl % G::NSLOT][b][r][4 * q], band_sel(in, b) + (zoff + ky) * cx + kx);
-      }
+      const long long zoff = (long long)pmod(kz0 - G::LH + pl, cz2) * cy * cx;
+      float* dst = &cw[pl % G::NSLOT][0][0][0];
+#pragma unroll
+      for (int c = 0; c < G::NCH; ++c)
+        if (soff[c] >= 0) cp_async16(dst + soff[c], gsrc[c] + zoff);
     }
     cp_async_commit();
   };
@@ -976,6 +985,7 @@ cudaError_t dwt3d_analysis_level(const float* in, int nx, int ny, int nz, float*
                                  const float* h, const float* g, int L, cudaStream_t st) {
   if (nx % 8 != 0 || ny % 2 != 0 || nz % 2 != 0 || !(L == 2 || L == 4 || L == 8) || !aligned16(in))
     return cudaErrorNotSupported;
+  if ((long long)nx * ny > 0x7fffffffLL) return cudaErrorNotSupported;  // in-plane offsets are int
   Bands8 b;
   for (int c = 0; c < 8; ++c) {
     if (!aligned16(bands[c])) return cudaErrorNotSupported;
@@ -991,6 +1001,7 @@ cudaError_t dwt3d_synthesis_level(const float* const bands[8], float wdet, int n
                                   const float* h, const float* g, int L, cudaStream_t st) {
   if (nx % 8 != 0 || ny % 2 != 0 || nz % 2 != 0 || !(L == 2 || L == 4 || L == 8) || !aligned16(out))
     return cudaErrorNotSupported;
+  if ((long long)nx * ny > 0x7fffffffLL) return cudaErrorNotSupported;  // in-plane offsets are int
   CBands8 b;
   for (int c = 0; c < 8; ++c) {
     if (!aligned16(bands[c])) return cudaErrorNotSupported;
