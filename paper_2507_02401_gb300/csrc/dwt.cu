@@ -207,6 +207,7 @@ struct A2F {
   static constexpr int WX = 2 * OX + HX;
   static constexpr int WY = 2 * OY + L - 2;
   static constexpr int NQ = WX / 4;
+  static constexpr int NCH = (WY * NQ + THREADS - 1) / THREADS;  // 16-byte chunks per thread and window
   static constexpr int WIN = WY * WX;  // floats per window buffer (multiple of 4)
   static constexpr int LOHI = WY * OX;
   static constexpr int SMEM = (2 * WIN + 2 * LOHI) * 4;
@@ -226,14 +227,23 @@ __global__ void __launch_bounds__(256) dwt2d_analysis_fast_kernel(const float* _
   const int t = threadIdx.x;
   griddep_wait();
   griddep_trigger();
+  // this thread's 16-byte chunks of a window: shared offset and (interior windows) source offset from the
+  // window corner are the same for every tile, so they are computed once
+  int soff[G::NCH], roff[G::NCH];
+#pragma unroll
+  for (int c = 0; c < G::NCH; ++c) {
+    const int i = t + c * G::THREADS;
+    const int r = i / G::NQ, q = i - r * G::NQ;
+    soff[c] = i < G::WY * G::NQ ? r * G::WX + 4 * q : -1;
+    roff[c] = r * nx + 4 * q;
+  }
   auto stage = [&](int tile, float* w) {
     const int kx0 = (tile % tiles_x) * G::OX, ky0 = (tile / tiles_x) * G::OY;
     if (2 * kx0 + G::WX <= nx && 2 * ky0 + G::WY <= ny) {  // interior window: no wrap
       const float* src = in + (long long)(2 * ky0) * nx + 2 * kx0;
-      for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
-        const int r = i / G::NQ, q = i - r * G::NQ;
-        cp_async16(w + r * G::WX + 4 * q, src + (long long)r * nx + 4 * q);
-      }
+#pragma unroll
+      for (int c = 0; c < G::NCH; ++c)
+        if (soff[c] >= 0) cp_async16(w + soff[c], src + roff[c]);
     } else {
       for (int i = t; i < G::WY * G::NQ; i += G::THREADS) {
         const int r = i / G::NQ, q = i - r * G::NQ;
@@ -319,13 +329,14 @@ struct S2F {
   static constexpr int NQ = WX / 4;
   static constexpr int K0 = (CX - LH) & ~1;        // first (even) window column a pixel quad reads
   static constexpr int NK2 = (CX + 2 - K0) / 2;    // float2 loads per pixel quad
+  static constexpr int NCH = (4 * WY * NQ + THREADS - 1) / THREADS;  // 16-byte chunks per thread and window
   static constexpr int WIN = 4 * WY * WX;          // floats per window buffer (four bands)
   static constexpr int LOHI = 2 * OY * WX;
   static constexpr int SMEM = (2 * WIN + 2 * LOHI) * 4;
 };
 
 template <int L>
-__global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* __restrict__ A,
+__global__ void __launch_bounds__(256, 4) dwt2d_synthesis_fast_kernel(const float* __restrict__ A,
                                                                    const float* __restrict__ Hb,
                                                                    const float* __restrict__ Vb,
                                                                    const float* __restrict__ Db, float wdet, int nx,
@@ -340,15 +351,37 @@ __global__ void __launch_bounds__(256) dwt2d_synthesis_fast_kernel(const float* 
   const int nx2 = nx >> 1, ny2 = ny >> 1;
   griddep_wait();
   griddep_trigger();
+  // this thread's 16-byte chunks of the four band windows: shared offset, and band (bits 28-29) with source
+  // offset from the window corner (interior windows), the same for every tile, so computed once
+  int soff[G::NCH], code[G::NCH];
+#pragma unroll
+  for (int c = 0; c < G::NCH; ++c) {
+    const int i = t + c * G::THREADS;
+    const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
+    const int r = rq / G::NQ, q = rq - r * G::NQ;
+    soff[c] = i < 4 * G::WY * G::NQ ? (b * G::WY + r) * G::WX + 4 * q : -1;
+    code[c] = (b << 28) | (r * nx2 + 4 * q);
+  }
   auto stage = [&](int tile, float* w) {
     const int kx0 = (tile % tiles_x) * G::OX, ky0 = (tile / tiles_x) * G::OY;
     const bool interior = kx0 >= G::CX && ky0 >= G::LH && kx0 + G::OX <= nx2 && ky0 + G::OY <= ny2;
+    if (interior) {
+      const long long corner = (long long)(ky0 - G::LH) * nx2 + kx0 - G::CX;
+#pragma unroll
+      for (int c = 0; c < G::NCH; ++c) {
+        if (soff[c] < 0) continue;
+        const int b = code[c] >> 28;
+        const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
+        cp_async16(w + soff[c], src + corner + (code[c] & 0x0fffffff));
+      }
+      return;
+    }
     for (int i = t; i < 4 * G::WY * G::NQ; i += G::THREADS) {
       const int b = i / (G::WY * G::NQ), rq = i - b * (G::WY * G::NQ);
       const int r = rq / G::NQ, q = rq - r * G::NQ;
       // periodic (a coarse level may be shorter than the halo: wrap repeatedly); nx2 % 4 == 0
-      const int ky = interior ? ky0 - G::LH + r : pmod(ky0 - G::LH + r, ny2);
-      const int kx = interior ? kx0 - G::CX + 4 * q : pmod(kx0 - G::CX + 4 * q, nx2);
+      const int ky = pmod(ky0 - G::LH + r, ny2);
+      const int kx = pmod(kx0 - G::CX + 4 * q, nx2);
       const float* src = b == 0 ? A : (b == 1 ? Hb : (b == 2 ? Vb : Db));
       cp_async16(w + (b * G::WY + r) * G::WX + 4 * q, src + (long long)ky * nx2 + kx);
     }
@@ -531,7 +564,7 @@ struct A3F {
 };
 
 template <int L>
-__global__ void __launch_bounds__(256, 3) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
+__global__ void __launch_bounds__(256, 2) dwt3d_analysis_fast_kernel(const float* __restrict__ in, int nx, int ny, int nz,
                                                                   const Bands8 out, float wdet, const Filt f,
                                                                   int cols_x, int ncols) {
   using G = A3F<L>;
@@ -676,7 +709,7 @@ struct S3F {
 // four zb = 1 bands gives two full-resolution planes P_lo(m), P_hi(m); output
 // plane 2m + e is then sum_jj h_{2jj+e} P_lo(m - jj) + g_{2jj+e} P_hi(m - jj).
 template <int L>
-__global__ void __launch_bounds__(256, 3) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
+__global__ void __launch_bounds__(256, 2) dwt3d_synthesis_fast_kernel(const CBands8 in, float wdet, int nx, int ny,
                                                                    int nz, float* __restrict__ out, const Filt f,
                                                                    int cols_x, int ncols) {
   using G = S3F<L>;
@@ -935,8 +968,9 @@ int grid1d(long long n) {
 cudaError_t dwt2d_analysis_level(const float* in, int nx, int ny, float* approx, float* bandH, float* bandV,
                                  float* bandD, float wdet, const float* h, const float* g, int L, cudaStream_t st) {
   const Filt f = make_filt(h, g, L);
-  if (nx % 8 == 0 && ny % 2 == 0 && aligned16(in) && aligned16(approx) && aligned16(bandH) && aligned16(bandV) &&
-      aligned16(bandD) && (L == 2 || L == 4 || L == 8)) {
+  // (nx bounded: the fast kernels keep in-window source offsets as int)
+  if (nx % 8 == 0 && nx <= (1 << 24) && ny % 2 == 0 && aligned16(in) && aligned16(approx) && aligned16(bandH) &&
+      aligned16(bandV) && aligned16(bandD) && (L == 2 || L == 4 || L == 8)) {
     if (L == 2) return launch_a2<2>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
     if (L == 4) return launch_a2<4>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
     return launch_a2<8>(st, in, nx, ny, approx, bandH, bandV, bandD, wdet, f);
@@ -950,8 +984,9 @@ cudaError_t dwt2d_synthesis_level(const float* approx, const float* bandH, const
                                   float wdet, int nx, int ny, float* out, const float* h, const float* g, int L,
                                   cudaStream_t st) {
   const Filt f = make_filt(h, g, L);
-  if (nx % 8 == 0 && ny % 2 == 0 && aligned16(approx) && aligned16(bandH) && aligned16(bandV) && aligned16(bandD) &&
-      aligned16(out) && (L == 2 || L == 4 || L == 8)) {
+  // (nx bounded: the fast kernels keep in-window source offsets as int, the band in bits 28-29)
+  if (nx % 8 == 0 && nx <= (1 << 24) && ny % 2 == 0 && aligned16(approx) && aligned16(bandH) && aligned16(bandV) &&
+      aligned16(bandD) && aligned16(out) && (L == 2 || L == 4 || L == 8)) {
     if (L == 2) return launch_s2<2>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
     if (L == 4) return launch_s2<4>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
     return launch_s2<8>(st, approx, bandH, bandV, bandD, wdet, nx, ny, out, f);
