@@ -157,9 +157,10 @@ bool tma3d_supported(int nx, int R, bool varc);
 // `cur` (80 x (16+2R) x 1 boxes) and `prev` (64 x 16 x 1) descriptors of an nx x ny x nz float field
 cudaError_t tma3d_encode(const float* base, int nx, int ny, int nz, int R, CUtensorMap* cur, CUtensorMap* prev);
 // Work split of a 3D TMA step launch: nctas = columns x nchunks CTAs, column-fastest, each a z range
-// of nz / nchunks planes.
+// of nz / nchunks planes; ring: the kernel form whose z queue is a register ring (one-wave grids).
 struct Tma3dSplit {
   int nctas, nchunks;
+  bool ring;
 };
 Tma3dSplit tma3d_split(int R, int nx, int ny, int nz);
 int tma3d_cta_of(int nx, int ny, int nz, const Tma3dSplit& sp, int x, int y, int z);  // CTA holding a cell

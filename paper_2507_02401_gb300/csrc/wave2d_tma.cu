@@ -62,9 +62,11 @@ struct G2 {
   static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + 16;
 };
 
-__device__ __forceinline__ void fused_sample2(const StepArgs& a, long long gtid) {
-  if (a.y == nullptr || gtid >= a.ns) return;
-  const int s = (int)gtid;
+// Sensor s = b + t * gridDim.x is sampled by thread t of CTA b (the sensors spread over every CTA).
+__device__ __forceinline__ void fused_sample2(const StepArgs& a, long long bid, int t) {
+  const long long gs = bid + (long long)t * gridDim.x;
+  if (a.y == nullptr || gs >= a.ns) return;
+  const int s = (int)gs;
   float v = 0.f;
   for (int k = 0; k < a.corners; ++k) v = fmaf(a.sens_w[s * a.corners + k], a.cur[a.sens_cell[s * a.corners + k]], v);
   a.y[(long long)s * a.nt + a.t_sample] = v;
@@ -88,7 +90,6 @@ __global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const Step
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + 2 * G::STAGE);
 
   const int t = threadIdx.x;
-  fused_sample2(a, (long long)blockIdx.x * THREADS + t);
 
   const int nx = a.nx, ny = a.ny;
   const int tiles_x = (nx + TX - 1) / TX;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(threads_of(MODE)) step2d_tma_kernel(const Step
   };
   int first = blockIdx.x;
   if (t == 0 && first < ntiles) issue(first, 0);
+  fused_sample2(a, blockIdx.x, t);  // while the first tile's boxes are in flight
 
   const float ckh = a.c_lap * a.kappa0, ckl = a.c_lap * a.kappa0_lo;
   float2 w2[R + 1];  // stencil weights, packed

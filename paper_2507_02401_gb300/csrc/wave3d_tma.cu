@@ -13,12 +13,13 @@
 // ring of shared-memory slots, PD planes ahead of the plane being computed,
 // plus the own 64 x 16 tile of `prev`; completion is tracked by one mbarrier
 // per slot.  Each thread owns 2 rows x 4 columns: x/y neighbours come from the
-// centre plane's slot, z neighbours from a register queue of 2R+1 planes.
+// centre plane's slot, z neighbours from a register ring of 2R+1 planes.
 // Compulsory DRAM traffic per point-update: cur and prev read once, next
 // written once (12 B); halo re-reads are served by L2.
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -42,18 +43,41 @@ struct G3 {
   static constexpr size_t SMEM = sizeof(float) * ((size_t)NS * PLANE + (size_t)NSP * PREV) + 8 * (NS + NSP);
 };
 
-__device__ __forceinline__ void fused_sample3(const StepArgs& a, long long gtid) {
-  if (a.y == nullptr || gtid >= a.ns) return;
-  const int s = (int)gtid;
+// Sensor s = b + t * gridDim.x is sampled by thread t of CTA b: the sensors are spread over every CTA
+// of the wave (a few per CTA) instead of loading the first CTAs with all of them.
+__device__ __forceinline__ void fused_sample3(const StepArgs& a, long long bid, int t) {
+  const long long gs = bid + (long long)t * gridDim.x;
+  if (a.y == nullptr || gs >= a.ns) return;
+  const int s = (int)gs;
   float v = 0.f;
   for (int k = 0; k < a.corners; ++k) v = fmaf(a.sens_w[s * a.corners + k], a.cur[a.sens_cell[s * a.corners + k]], v);
   a.y[(long long)s * a.nt + a.t_sample] = v;
 }
 
+// Runs f(S, i + S) for S = 0 .. Q-1 while i + S < n (S a compile-time constant in each call); false as
+// soon as one call returns false.
+template <int S, int Q, class F>
+__device__ __forceinline__ bool march(F& f, int i, int n) {
+  if constexpr (S == Q) {
+    return true;
+  } else {
+    if (i + S >= n) return true;
+    if (!f(std::integral_constant<int, S>{}, i + S)) return false;
+    return march<S + 1, Q>(f, i, n);
+  }
+}
+
+// The adjoint's injection S^T r_m into one cell: sum of w r_m over the cell's sensor entries.
+__device__ __forceinline__ float inj_sum(const StepArgs& a, const InjCell& c) {
+  float v = 0.f;
+  for (int q = c.beg; q < c.end; ++q) v = fmaf(a.ent_w[q], a.inj_r[(long long)a.ent_sensor[q] * a.nt + a.inj_t], v);
+  return v;
+}
+
 // INJ: the adjoint's injection S^T r_m into the CTA's own cells of `next` after the step (per-CTA lists)
 // Work split (column-fastest): CTA b takes column b mod columns and the (b div columns)-th of
 // nchunks equal z ranges, so CTAs that run together stream neighbouring columns of the same rows.
-template <int R, bool INJ>
+template <int R, bool INJ, bool RING>
 __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap mcur,
                                                              const __grid_constant__ CUtensorMap mprev, int cols_x,
                                                              int nchunks, int* status, long long timeout_ns) {
@@ -66,7 +90,6 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
 
   const int t = threadIdx.x;
   const long long bid = blockIdx.x;
-  fused_sample3(a, bid * THREADS + t);
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = (long long)nx * ny;
@@ -111,8 +134,9 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
     if (has_prev)
       for (int j = 0; j < min(PD, nloc); ++j) issue_prev(j);
   }
+  fused_sample3(a, bid, t);  // the forward's sensor samples of cur, while the first copies are in flight
 
-  // register queue of the own cells: q[i] = plane z - R + i
+  // register ring of the own cells: at the first plane q[k] = plane z0 - R + k
   float4 q[2 * R + 1][2];
 #pragma unroll
   for (int i = 0; i < R; ++i)  // planes z0-R .. z0-1 straight from global memory
@@ -132,7 +156,13 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
       q[R + i][rr] = *reinterpret_cast<const float4*>(ring + (i % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
   }
 
-  for (int i = 0; i < nloc; ++i) {
+  // One plane of the march.  RING: the z queue is a ring in registers, logical entry k (plane z - R + k)
+  // of plane i sitting in q[(k + i) % Q]; the loop is unrolled Q times, so S = i % Q is a compile-time
+  // constant in every copy and no queue entry moves between registers (fewer instructions, a Q times
+  // larger loop body).  Otherwise S = 0 and the queue shifts after every plane.
+  constexpr int Q = 2 * R + 1;
+  auto step = [&](auto sc, int i) -> bool {
+    constexpr int S = decltype(sc)::value;
     if (t == 0) {
       fence_proxy_async_shared();  // the slots refilled below were last read through the generic proxy
       if (i + R + PD < ncur) issue_cur(i + R + PD);
@@ -143,12 +173,12 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
     if (has_prev) good = good && mbar_wait(&pbars[i % G::NSP], (i / G::NSP) & 1, timeout_ns);
     if (__syncthreads_or(!good)) {
       if (t == 0) atomicCAS(status, (int)PAT_OK, (int)PAT_ERR_TIMEOUT);
-      ok_all = false;
-      break;
+      return false;
     }
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr)
-      q[2 * R][rr] = *reinterpret_cast<const float4*>(ring + (jq % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
+      q[(2 * R + S) % Q][rr] =
+          *reinterpret_cast<const float4*>(ring + (jq % G::NS) * G::PLANE + (r0 + rr + R) * BW + XH + c0);
 
     const float* cen = ring + (i % G::NS) * G::PLANE;
     float2 L[2][2];  // packed pairs: cells (2p, 2p+1) of row rr
@@ -161,12 +191,12 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
       float2 out[2];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const float2 c = p ? hi2(q[R][rr]) : lo2(q[R][rr]);
+        const float2 c = p ? hi2(q[(R + S) % Q][rr]) : lo2(q[(R + S) % Q][rr]);
         float2 acc = L[rr][p];
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
-          const float2 up = p ? hi2(q[R + m][rr]) : lo2(q[R + m][rr]);
-          const float2 dn = p ? hi2(q[R - m][rr]) : lo2(q[R - m][rr]);
+          const float2 up = p ? hi2(q[(R + m + S) % Q][rr]) : lo2(q[(R + m + S) % Q][rr]);
+          const float2 dn = p ? hi2(q[(R - m + S) % Q][rr]) : lo2(q[(R - m + S) % Q][rr]);
           acc = __ffma2_rn(w2[m], __ffma2_rn(c, m2, __fadd2_rn(up, dn)), acc);
         }
         // c_cur c - c_prev prev + (ck + ckl) acc, the last product rounded once
@@ -179,22 +209,32 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
         *reinterpret_cast<float4*>(a.next + z * plane + (long long)gy * nx + gx) =
             make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
     }
+    __syncthreads();  // the centre slot is refilled by the next step's TMA
+    return true;
+  };
+  if constexpr (RING) {
+    for (int i = 0; i < nloc; i += Q)
+      if (!march<0, Q>(step, i, nloc)) {
+        ok_all = false;
+        break;
+      }
+  } else {  // the queue shifts by one plane after every step (one copy of the loop body)
+    for (int i = 0; i < nloc; ++i) {
+      if (!step(std::integral_constant<int, 0>{}, i)) {
+        ok_all = false;
+        break;
+      }
 #pragma unroll
-    for (int k = 0; k < 2 * R; ++k) {
-      q[k][0] = q[k + 1][0];
-      q[k][1] = q[k + 1][1];
+      for (int k = 0; k < 2 * R; ++k) {
+        q[k][0] = q[k + 1][0];
+        q[k][1] = q[k + 1][1];
+      }
     }
-    __syncthreads();  // the centre slot is refilled by the next iteration's TMA
   }
   if (INJ && ok_all) {  // every thread's stores to `next` precede the injection (same CTA)
     __syncthreads();
-    for (int e = a.inj_tile_ptr[bid] + t; e < a.inj_tile_ptr[bid + 1]; e += THREADS) {
-      const InjCell c = a.inj_tile[e];
-      float v = 0.f;
-      for (int q = c.beg; q < c.end; ++q)
-        v = fmaf(a.ent_w[q], a.inj_r[(long long)a.ent_sensor[q] * a.nt + a.inj_t], v);
-      a.next[c.local] += v;
-    }
+    for (int e = a.inj_tile_ptr[bid] + t; e < a.inj_tile_ptr[bid + 1]; e += THREADS)
+      a.next[a.inj_tile[e].local] += inj_sum(a, a.inj_tile[e]);
   }
   // after a timed-out wait: give the copies still in flight (the last one of
   // each slot) a bounded chance to land before the CTA's shared memory goes away
@@ -205,51 +245,62 @@ __global__ void __launch_bounds__(THREADS) step3d_tma_kernel(const StepArgs a, c
   }
 }
 
-template <int R, bool INJ>
+template <int R, bool INJ, bool RING>
 cudaError_t prepare_r() {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(step3d_tma_kernel<R, INJ, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)G3<R>::SMEM);
   });
   return attr_err;
 }
 
-template <int R, bool INJ>
+template <int R, bool INJ, bool RING>
 cudaError_t launch_r(const StepArgs& a, const CUtensorMap& mc, const CUtensorMap& mp, int nctas, int nchunks,
                      int* status, long long timeout_ns, cudaStream_t st) {
-  const cudaError_t attr_err = prepare_r<R, INJ>();
+  const cudaError_t attr_err = prepare_r<R, INJ, RING>();
   if (attr_err != cudaSuccess) return attr_err;
-  step3d_tma_kernel<R, INJ><<<nctas, THREADS, G3<R>::SMEM, st>>>(a, mc, mp, (a.nx + TX - 1) / TX, nchunks, status,
-                                                                  timeout_ns);
+  step3d_tma_kernel<R, INJ, RING><<<nctas, THREADS, G3<R>::SMEM, st>>>(a, mc, mp, (a.nx + TX - 1) / TX, nchunks,
+                                                                        status, timeout_ns);
   return cudaGetLastError();
 }
 
-// Co-resident CTAs of the step kernel (both variants) on the current device.
-template <int R>
-int resident_r() {
-  int dev = 0, sms = 0, pf = 0, pi = 0;
-  if (prepare_r<R, false>() != cudaSuccess || prepare_r<R, true>() != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, step3d_tma_kernel<R, false>, THREADS, G3<R>::SMEM) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pi, step3d_tma_kernel<R, true>, THREADS, G3<R>::SMEM) !=
+template <int R, bool INJ, bool RING>
+int blocks_per_sm() {
+  int per = 0;
+  if (prepare_r<R, INJ, RING>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step3d_tma_kernel<R, INJ, RING>, THREADS, G3<R>::SMEM) !=
           cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return sms * (pf < pi ? pf : pi);
+  return per;
 }
 
-template <bool INJ>
+// Co-resident CTAs of the step kernel (every variant) on the current device.
+template <int R>
+int resident_r() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int v[4] = {blocks_per_sm<R, false, false>(), blocks_per_sm<R, true, false>(), blocks_per_sm<R, false, true>(),
+                    blocks_per_sm<R, true, true>()};
+  int per = v[0];
+  for (int i = 1; i < 4; ++i) per = v[i] < per ? v[i] : per;
+  return sms * per;
+}
+
+template <bool INJ, bool RING>
 cudaError_t launch_i(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev, int nctas,
                      int nchunks, int* status, long long timeout_ns, cudaStream_t st) {
   switch (R) {
-    case 1: return launch_r<1, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
-    case 3: return launch_r<3, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
-    case 5: return launch_r<5, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
-    case 7: return launch_r<7, INJ>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 1: return launch_r<1, INJ, RING>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 3: return launch_r<3, INJ, RING>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 5: return launch_r<5, INJ, RING>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
+    case 7: return launch_r<7, INJ, RING>(a, cur, prev, nctas, nchunks, status, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -323,7 +374,10 @@ Tma3dSplit tma3d_split(int R, int nx, int ny, int nz) {
     chunks = (nz + zc - 1) / zc;
   }
   if (chunks > nz) chunks = nz;
-  return Tma3dSplit{(int)(cols * chunks), chunks};
+  // the register-ring march saves the queue's register moves where issue is the bound (one-wave grids:
+  // 38.7 / 40.3 us against 39.4 / 41.2 per K / K* step at 256^3), but its larger body costs where DRAM is
+  // (many columns: 274.5 / 278.7 us against 264.8 / 268.9 at 512^3)
+  return Tma3dSplit{(int)(cols * chunks), chunks, cols * 4 < cap};
 }
 
 // CTA holding cell (x, y, z) (the kernel's split: chunk zr holds z in [zr nz / k, (zr + 1) nz / k)).
@@ -341,8 +395,11 @@ long long tma3d_threads(int nctas) { return (long long)nctas * THREADS; }
 
 cudaError_t step3d_tma_launch(int R, const StepArgs& a, const CUtensorMap& cur, const CUtensorMap& prev,
                               const Tma3dSplit& sp, int* status, long long timeout_ns, cudaStream_t st) {
-  return a.inj_r ? launch_i<true>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st)
-                 : launch_i<false>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st);
+  if (sp.ring)
+    return a.inj_r ? launch_i<true, true>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st)
+                   : launch_i<false, true>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st);
+  return a.inj_r ? launch_i<true, false>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st)
+                 : launch_i<false, false>(R, a, cur, prev, sp.nctas, sp.nchunks, status, timeout_ns, st);
 }
 
 }  // namespace pat
