@@ -691,6 +691,106 @@ __global__ void __launch_bounds__(256, 2) dwt3d_analysis_fast_kernel(const float
   }  // runs
 }
 
+// Plane-parallel form of a 3D analysis level, for levels whose (column,
+// output plane) items fit in one wave of CTAs: a CTA makes one output plane
+// m of one column, staging all L input planes 2m .. 2m + L - 1 (periodic) at
+// once and filtering them along x, then y, then z.  One staging round trip
+// and two barriers instead of L serial plane steps; the passes are the
+// marching kernel's, in the same tap order, so the bands are identical.
+template <int L>
+struct A3P {
+  static constexpr int OX = 32, OY = 8, THREADS = 256;
+  static constexpr int HX = (L - 2 + 3) / 4 * 4;
+  static constexpr int WX = 2 * OX + HX;
+  static constexpr int WXP = pad_row(WX);
+  static constexpr int WY = 2 * OY + L - 2;
+  static constexpr int NQ = WX / 4;
+  static constexpr int NCH = (WY * NQ + THREADS - 1) / THREADS;
+  static constexpr int SLAB_BYTES = L * WY * WXP * 4;
+  static constexpr int X_BYTES = WY * OX * 4;
+  static constexpr int SMEM = SLAB_BYTES + 2 * L * X_BYTES;  // L staged planes; x-low and x-high of each
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt3d_analysis_pp_kernel(const float* __restrict__ in, int nx, int ny, int nz,
+                                                                const Bands8 out, float wdet, const Filt f,
+                                                                int cols_x, int ncols) {
+  using G = A3P<L>;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  auto slab = reinterpret_cast<float(*)[G::WY][G::WXP]>(dsm);                 // [plane]
+  auto xbuf = reinterpret_cast<float(*)[G::WY][G::OX]>(dsm + G::SLAB_BYTES);  // [2 plane + xb]
+  const int t = threadIdx.x;
+  const int nx2 = nx >> 1, ny2 = ny >> 1;
+  const int col = (int)(blockIdx.x % ncols), m = (int)(blockIdx.x / ncols);
+  const int kx0 = (col % cols_x) * G::OX, ky0 = (col / cols_x) * G::OY;
+  griddep_wait();
+  griddep_trigger();
+#pragma unroll
+  for (int c = 0; c < G::NCH; ++c) {
+    const int i = t + c * G::THREADS;
+    if (i >= G::WY * G::NQ) break;
+    const int r = i / G::NQ, q = i - r * G::NQ;
+    const int soff = r * G::WXP + 4 * q;
+    const int goff = ((2 * ky0 + r) % ny) * nx + (2 * kx0 + 4 * q) % nx;  // nx % 4 == 0: no chunk straddles the wrap
+#pragma unroll
+    for (int p = 0; p < L; ++p) {
+      int z = 2 * m + p;
+      while (z >= nz) z -= nz;
+      cp_async16(&slab[p][0][0] + soff, in + (long long)z * ny * nx + goff);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait_group<0>();
+  __syncthreads();
+  for (int i = t; i < L * G::WY * (G::OX / 4); i += G::THREADS) {  // along x, every plane
+    const int p = i / (G::WY * (G::OX / 4)), ri = i - p * (G::WY * (G::OX / 4));
+    const int r = ri / (G::OX / 4), q = ri - r * (G::OX / 4);
+    float v[8 + G::HX];
+#pragma unroll
+    for (int c = 0; c < (8 + G::HX) / 4; ++c) {
+      const float4 w4 = *reinterpret_cast<const float4*>(&slab[p][r][8 * q + 4 * c]);
+      v[4 * c] = w4.x;
+      v[4 * c + 1] = w4.y;
+      v[4 * c + 2] = w4.z;
+      v[4 * c + 3] = w4.w;
+    }
+    float sl[4], sh[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sl[k] = 0.f;
+      sh[k] = 0.f;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        sl[k] = fmaf(f.h[j], v[2 * k + j], sl[k]);
+        sh[k] = fmaf(f.g[j], v[2 * k + j], sh[k]);
+      }
+    }
+    *reinterpret_cast<float4*>(&xbuf[2 * p][r][4 * q]) = make_float4(sl[0], sl[1], sl[2], sl[3]);
+    *reinterpret_cast<float4*>(&xbuf[2 * p + 1][r][4 * q]) = make_float4(sh[0], sh[1], sh[2], sh[3]);
+  }
+  __syncthreads();
+  // along y (this thread's quarter qq, row ky, columns 4 qx ..), then along z over the L planes
+  const int qq = t / 64, ky = (t / 8) % 8, qx = t % 8;
+  const int xb = qq & 1, yb = qq >> 1;
+  F4x2 lo, hi;
+#pragma unroll
+  for (int p = 0; p < L; ++p) {
+    F4x2 v;
+#pragma unroll
+    for (int j = 0; j < L; ++j) v.fma(dup2(yb ? f.g[j] : f.h[j]), F4x2::ld(&xbuf[2 * p + xb][2 * ky + j][4 * qx]));
+    lo.fma(dup2(f.h[p]), v);
+    hi.fma(dup2(f.g[p]), v);
+  }
+  const int oy = ky0 + ky, ox = kx0 + 4 * qx;
+  if (oy < ny2 && ox < nx2) {
+    float* plo = qq == 0 ? out.p[0] : qq == 1 ? out.p[1] : qq == 2 ? out.p[2] : out.p[3];
+    float* phi = qq == 0 ? out.p[4] : qq == 1 ? out.p[5] : qq == 2 ? out.p[6] : out.p[7];
+    const long long o = ((long long)m * ny2 + oy) * nx2 + ox;
+    lo.scale(dup2(qq == 0 ? 1.f : wdet)).st(plo + o);
+    hi.scale(dup2(wdet)).st(phi + o);
+  }
+}
+
 template <int L>
 struct S3F {
   static constexpr int OX = 32, OY = 8, THREADS = 256, NSLOT = 3;  // coefficient block; 2 OX x 2 OY pixels
@@ -859,11 +959,18 @@ cudaError_t launch_a3(cudaStream_t st, const float* in, int nx, int ny, int nz, 
                       const Filt& f) {
   static std::once_flag once;
   static int cap = 0;
-  std::call_once(once, [] { cap = resident_ctas((const void*)dwt3d_analysis_fast_kernel<L>, A3F<L>::SMEM); });
+  static int cap_pp = 0;
+  std::call_once(once, [] {
+    cap = resident_ctas((const void*)dwt3d_analysis_fast_kernel<L>, A3F<L>::SMEM);
+    cap_pp = resident_ctas((const void*)dwt3d_analysis_pp_kernel<L>, A3P<L>::SMEM);
+  });
   if (cap <= 0) return cudaErrorInvalidConfiguration;
   const int cols_x = ((nx >> 1) + A3F<L>::OX - 1) / A3F<L>::OX;
   const int ncols = cols_x * (((ny >> 1) + A3F<L>::OY - 1) / A3F<L>::OY);
   const long long work = (long long)ncols * (nz >> 1);
+  if (work <= cap_pp)  // every (column, output plane) item in one wave: no serial plane march
+    return launch_pdl(dwt3d_analysis_pp_kernel<L>, (int)work, A3P<L>::SMEM, st, in, nx, ny, nz, b, wdet, f, cols_x,
+                      ncols);
   return launch_pdl(dwt3d_analysis_fast_kernel<L>, grid3d(work, cap), A3F<L>::SMEM, st, in, nx, ny, nz, b, wdet, f,
                     cols_x, ncols);
 }

@@ -96,11 +96,13 @@ def test_sensors_on_cells_and_edges():
 # level, 3D fused level with z-marching); narrower levels the generic ones: the cases mix both, with
 # ragged CTA blocks (coefficient widths not multiples of the 64 x 16 / 32 x 8 blocks), several CTAs per
 # axis and per z chunk, coarse levels shorter than the filter halo (periodic wrap repeated), and 3D
-# levels with many columns and few planes (a CTA's share of the work spans several columns).
+# levels with many columns and few planes (a CTA's share of the work spans several columns).  3D levels
+# whose (column, output plane) items fit in one wave take the plane-parallel kernel, larger ones the
+# z-marching kernel (the last three cases, the last with ragged column blocks).
 WAVELET_CASES = [((64, 64), 1, 3), ((64, 64), 2, 3), ((128, 64), 4, 5), ((16, 16), 4, 4), ((32, 32, 32), 4, 3),
                  ((16, 8, 8), 2, 2), ((512, 512), 4, 5), ((72, 1032), 4, 3), ((264, 136), 2, 3), ((16, 64), 4, 3),
                  ((8, 256), 4, 3), ((24, 40, 48), 4, 2), ((32, 24, 136), 4, 2), ((64, 64, 64), 4, 4),
-                 ((16, 16, 72), 1, 3), ((8, 512, 1024), 4, 2), ((32, 256, 1024), 4, 2)]
+                 ((16, 16, 72), 1, 3), ((8, 512, 1024), 4, 2), ((32, 256, 1024), 4, 2), ((16, 328, 1032), 4, 2)]
 
 
 @pytest.mark.parametrize("shape,family,levels", WAVELET_CASES)
