@@ -13,7 +13,8 @@
 // HBM-rate kernels (16-byte cp.async staging with the periodic wrap computed
 // per 16-byte chunk, float4 band stores); narrower levels take the generic
 // kernels.  3D levels with width a multiple of 8 run as one fused pass
-// (x/y in shared memory, z from a register ring while marching through z);
+// (x/y in shared memory, z in registers while marching through z, or all
+// planes of an output plane at once on levels that fit one wave of CTAs);
 // other 3D levels run as separable 1D passes.
 #include <mutex>
 
@@ -534,10 +535,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // One pass per level: a CTA owns an OX x OY block of coefficient columns and
 // marches through a chunk of z planes.  Each input plane's window is staged
 // by cp.async (NSLOT - 1 planes ahead), filtered along x and y in shared
-// memory into the four (x, y) quarters; each thread keeps its quarter values
-// of the last L planes in registers and applies the z filter every second
-// plane, writing the eight bands (code = zb << 2 | yb << 1 | xb; code 0 is the
-// approximation) with float4 stores.
+// memory into the four (x, y) quarters; each thread folds its quarter values
+// of every plane into register accumulators of the L/2 output planes that
+// plane reaches (low and high along z, taps in tap order) and writes the
+// finished output plane after every second input plane: the eight bands
+// (code = zb << 2 | yb << 1 | xb; code 0 is the approximation) with float4
+// stores.  The staging chunks' offsets are computed once per run of planes.
 struct Bands8 {
   float* p[8];
 };
