@@ -133,6 +133,9 @@ def test_tree_256_cubed_800_steps():
     assert e_kt <= TOL_OP
     x = w.x_true
     assert rel(plan.EsT(x, 1.0).cpu().numpy(), wav.EsT(x, 1.0)) <= TOL_OP
+    # the synthesis E_s at the full size too (E_s* above: z-marching levels 1-2, plane-parallel 3-4)
+    u = np.random.default_rng(80).standard_normal(x.size)
+    assert rel(plan.Es(u, 1.0).cpu().numpy(), wav.Es(u, 1.0)) <= TOL_OP
     plan.close()
 
 
