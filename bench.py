@@ -33,9 +33,9 @@ on a grid twice as fine, one step = one 15-iteration GMRES reconstruction.
 (2D 2048^2 .. 16384^2 x orders {2, 8}, 4096^2 order 8 with a varying medium
 and with a 10-cell absorbing layer, 3D 256^3 and 512^3 order 4).
 
---impl reference runs the FP64 CPU oracle (the reference arm of this
-build): each step is one oracle CG iteration of the same workload (for the
-volume, one K + K* pair at 40 steps scaled linearly to the full 800).
+--impl reference runs the FP64 CPU oracle (the reference arm): each step is
+one oracle CG iteration of the same workload (for the volume, one K + K*
+pair at 40 steps scaled linearly to the full 800).
 """
 import argparse
 import csv

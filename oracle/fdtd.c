@@ -23,7 +23,7 @@
  * with the standard staggered Fornberg weights c_k; -G^T is the matching
  * divergence.  Faces exist wherever they can touch an interior cell.
  *
- * Absorbing layer (optional; the build's reading of the paper's PML, which the
+ * Absorbing layer (optional; this implementation's reading of the paper's PML, which the
  * paper takes from k-Wave): a damping rate sigma(x) >= 0 [1/s] enters the
  * pressure equation, p_t + sigma p = -c^2 div v, with sigma p averaged over
  * the two time levels (trapezoidal rule):

@@ -140,7 +140,7 @@ class Wave:
 
 
 def sponge_sigma(shape, width, sigma_max):
-    """Damping rate of the absorbing layer (the build's reading of the paper's
+    """Damping rate of the absorbing layer (this implementation's reading of the paper's
     PML): within `width` cells of each grid face, sigma grows quadratically
     from 0 (at `width` cells from the face) to sigma_max (on the face); the
     contributions of the axes add up, so corners are damped twice.  For a

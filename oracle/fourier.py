@@ -3,7 +3,7 @@
 Paper Sec. 4 (implementation): the adjoint embedding acts in the Fourier
 domain as multiplication by the Bessel potential (1 + 4 pi^2 |xi|^2)^{-s},
 E_s* X = ifft(B . fft(X)) with B that potential sampled on the discrete
-frequencies.  In the coefficient formulation of this build (H = E_s* K* K E_s
+frequencies.  In the coefficient formulation used here (H = E_s* K* K E_s
 + alpha I, x = E_s u) the paper's operator is the covariance Gamma = E_s E_s*,
 so the Fourier prior's E_s is the filter with the square root of the
 potential, (1 + 4 pi^2 |xi|^2)^{-s/2}; it is real and symmetric, so E_s* = E_s.

@@ -1,4 +1,4 @@
-"""Pins of the oracle's absorbing layer (the build's reading of the paper's
+"""Pins of the oracle's absorbing layer (this implementation's reading of the paper's
 PML: damping sigma p in the pressure equation, trapezoidal in time; see
 oracle/fdtd.c): sigma = 0 is the undamped program, a uniform sigma on a
 Dirichlet sine mode follows the closed form of the damped three-level
