@@ -17,6 +17,7 @@
 // planes of an output plane at once on levels that fit one wave of CTAs);
 // other 3D levels run as separable 1D passes.
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -794,6 +795,18 @@ __global__ void __launch_bounds__(256) dwt3d_analysis_pp_kernel(const float* __r
   }
 }
 
+// Runs f(S, i + S) for S = 0 .. Q-1 while i + S < n (S a compile-time constant in each call).
+template <int S, int Q, class F>
+__device__ __forceinline__ bool march3(F& f, int i, int n) {
+  if constexpr (S == Q) {
+    return true;
+  } else {
+    if (i + S >= n) return true;
+    if (!f(std::integral_constant<int, S>{}, i + S)) return false;
+    return march3<S + 1, Q>(f, i, n);
+  }
+}
+
 template <int L>
 struct S3F {
   static constexpr int OX = 32, OY = 8, THREADS = 256, NSLOT = 3;  // coefficient block; 2 OX x 2 OY pixels
@@ -863,7 +876,12 @@ __global__ void __launch_bounds__(256, 2) dwt3d_synthesis_fast_kernel(const CBan
   float4 rlo[L / 2], rhi[L / 2];  // P_lo, P_hi of the last L/2 coefficient planes, oldest first
 #pragma unroll
   for (int j = 0; j < L / 2; ++j) rlo[j] = rhi[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int pl = 0; pl < nplanes; ++pl) {
+  // one coefficient plane; the z ring is rotated, not shifted: logical entry k (k = 0 oldest) of plane pl
+  // sits in rlo/rhi[(k + pl) % NRG], and the loop below is unrolled NRG times so that S = pl % NRG is a
+  // compile-time constant in every copy
+  constexpr int NRG = L / 2;
+  auto plane_step = [&](auto sc, int pl) -> bool {
+    constexpr int S = decltype(sc)::value;
     load(pl + G::NSLOT - 1);
     cp_async_wait_group<G::NSLOT - 1>();
     __syncthreads();
@@ -926,13 +944,8 @@ __global__ void __launch_bounds__(256, 2) dwt3d_synthesis_fast_kernel(const CBan
       }
       P[zb] = make_float4(v[0], v[1], v[2], v[3]);
     }
-#pragma unroll
-    for (int j = 0; j < L / 2 - 1; ++j) {
-      rlo[j] = rlo[j + 1];
-      rhi[j] = rhi[j + 1];
-    }
-    rlo[L / 2 - 1] = P[0];
-    rhi[L / 2 - 1] = P[1];
+    rlo[(NRG - 1 + S) % NRG] = P[0];  // the newest plane replaces the oldest
+    rhi[(NRG - 1 + S) % NRG] = P[1];
     if (pl >= G::LH) {  // rings hold coefficient planes m - LH .. m: output planes 2m, 2m + 1
       const int m = kz0 + pl - G::LH;
       const int iy = 2 * ky0 + pr, ix = 2 * kx0 + 4 * pq;
@@ -943,17 +956,19 @@ __global__ void __launch_bounds__(256, 2) dwt3d_synthesis_fast_kernel(const CBan
         for (int jj = 0; jj < L / 2; ++jj) {
           const int j = 2 * jj + e;
           F4x2 a, b;
-          a.p0 = make_float2(rlo[L / 2 - 1 - jj].x, rlo[L / 2 - 1 - jj].y);
-          a.p1 = make_float2(rlo[L / 2 - 1 - jj].z, rlo[L / 2 - 1 - jj].w);
-          b.p0 = make_float2(rhi[L / 2 - 1 - jj].x, rhi[L / 2 - 1 - jj].y);
-          b.p1 = make_float2(rhi[L / 2 - 1 - jj].z, rhi[L / 2 - 1 - jj].w);
+          a.p0 = make_float2(rlo[(NRG - 1 - jj + S) % NRG].x, rlo[(NRG - 1 - jj + S) % NRG].y);
+          a.p1 = make_float2(rlo[(NRG - 1 - jj + S) % NRG].z, rlo[(NRG - 1 - jj + S) % NRG].w);
+          b.p0 = make_float2(rhi[(NRG - 1 - jj + S) % NRG].x, rhi[(NRG - 1 - jj + S) % NRG].y);
+          b.p1 = make_float2(rhi[(NRG - 1 - jj + S) % NRG].z, rhi[(NRG - 1 - jj + S) % NRG].w);
           v.fma(dup2(f.h[j]), a);
           v.fma(dup2(f.g[j]), b);
         }
         if (iy < ny && ix < nx) v.st(out + ((long long)(2 * m + e) * ny + iy) * nx + ix);
       }
     }
-  }
+    return true;
+  };
+  for (int pl = 0; pl < nplanes; pl += NRG) march3<0, NRG>(plane_step, pl, nplanes);
   }  // runs
 }
 
